@@ -1,0 +1,191 @@
+/*
+ * hotrg.h -- C ABI of libhotrg: HOTRG coarse-graining of the 2D generalized
+ * XY model (q = 2) on one NVIDIA B300 (sm_103a).
+ *
+ * The method is the higher-order tensor renormalization group of the thesis
+ * "Numerical Investigations of Phase Transitions in Lattice Field Theories",
+ * §2.4.1 (Eq. 2.11 fuse, Eq. 2.12 HOSVD, the eps_1/eps_2 rule and Eq. 2.15
+ * projector, Eq. 2.16 coarse tensor), applied to the character-expanded
+ * generalized XY tensor of §3.2-§3.3 (Eq. 3.4 coefficients a_n, Eq. 3.6 /
+ * 3.15 site tensor) with the impurity tensors of §3.4 (Eq. 3.20, 3.21).
+ *
+ * Conventions common to every entry point
+ *   - Every call returns a hotrg_status and never aborts, traps or throws.
+ *     On a status other than HOTRG_OK the outputs are undefined and
+ *     hotrg_last_error(ctx) returns a one-line description.
+ *   - Tensors are row-major FP64 with legs [l][r][u][d] (left, right, up,
+ *     down; d fastest).  Bond-state labels are int32: the U(1) charge
+ *     n = i - n_max at zero field, the charge parity with h1 only (h = 0),
+ *     0 when h != 0 (no block structure).
+ *   - Pointers documented as "device" are caller-owned device memory
+ *     (cudaMalloc or a framework allocator); "host" pointers are ordinary
+ *     host memory.  The library owns only the workspace inside hotrg_ctx.
+ *   - All device work is enqueued on the stream given to hotrg_create.
+ *     hotrg_init_tensor and hotrg_step are asynchronous with respect to the
+ *     host except for the error checks noted; hotrg_run and
+ *     hotrg_observables return after their host outputs are written.
+ *   - One hotrg_ctx per host thread; a context is not thread-safe.
+ *   - Precision forms: HOTRG_FP64 computes every contraction with FP64
+ *     fused multiply-adds.  HOTRG_SPLIT_BF16 computes the environment and
+ *     coarse contractions on the tensor cores from fixed-point BF16 slices
+ *     of the FP64 operands (exact FP32 accumulation of slice products,
+ *     FP64 recombination), keeping the eigensolve, normalisation and ln Z
+ *     in FP64.  HOTRG_3XTF32 is the three-product TF32 split with FP32
+ *     accumulation.
+ */
+#ifndef HOTRG_H
+#define HOTRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HOTRG_MAX_STEPS 64
+
+typedef struct hotrg_ctx hotrg_ctx; /* opaque; owns device workspace */
+
+typedef enum {
+    HOTRG_OK = 0,
+    HOTRG_EINVAL = -1,   /* invalid argument (sizes, parameters, null pointer) */
+    HOTRG_ENOMEM = -2,   /* device or host allocation failed */
+    HOTRG_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
+    HOTRG_ENOCONV = -4,  /* eigensolver did not converge within its sweep cap */
+    HOTRG_ETIMEOUT = -5, /* a bounded device wait ran out */
+    HOTRG_ENOTSUP = -6   /* form not available in this build / on this device */
+} hotrg_status;
+
+typedef enum { HOTRG_FP64 = 0, HOTRG_SPLIT_BF16 = 1, HOTRG_3XTF32 = 2 } hotrg_prec;
+
+typedef enum {
+    HOTRG_T_PURE = 0,   /* Eq. 3.15: sqrt(a_l a_r a_u a_d) * sum_j I_{Q+2j}(bh) I_j(bh1) */
+    HOTRG_T_IMP_M = 1,  /* Eq. 3.20: cos(theta) impurity */
+    HOTRG_T_IMP_M1 = 2, /* Eq. 3.21: cos(2 theta) impurity */
+    HOTRG_T_ISING = 3   /* 2D Ising tensor (bond dimension 2), a test model */
+} hotrg_tkind;
+
+/* Parameters of one (beta, Delta) point. */
+typedef struct {
+    double beta;         /* inverse temperature, > 0 */
+    double delta;        /* Delta in [0, 1]: J = Delta, J1 = 1 - Delta (Eq. 3.1) */
+    double h;            /* field on cos(theta), >= 0 (Eq. 3.7) */
+    double h1;           /* field on cos(2 theta), >= 0 (Eq. 3.7) */
+    int32_t n_max;       /* Fourier cutoff: D0 = 2 n_max + 1, 0 <= n_max <= 64 */
+    int32_t d_cut;       /* bond-dimension cap D_cut, 1 <= d_cut <= 128 */
+    int32_t n_steps;     /* coarse-graining steps, one axis each: N = 2^n_steps sites */
+    int32_t prec;        /* hotrg_prec */
+    int32_t env_policy;  /* 0: compare eps_1 and eps_2 (§2.4.1); 1: left side only */
+    int32_t m_range;     /* Bessel-sum range m in [-m_range, m_range]; the thesis uses 50 */
+    int32_t eig_max_sweeps; /* Jacobi sweep cap (default 40 when <= 0) */
+    int32_t tkind;       /* hotrg_tkind of the pure tensor: HOTRG_T_PURE or HOTRG_T_ISING */
+    double tie_rtol;     /* cut-cluster width relative to lambda_max (default 1e-12 when <= 0) */
+    double eig_tol;      /* Jacobi stop: off-diagonal Frobenius <= eig_tol * ||E_q||_F (1e-15 when <= 0) */
+} hotrg_params;
+
+/* Per-step scalars (device- or host-resident, see each entry point). */
+typedef struct {
+    double ln_c;       /* ln of the Frobenius norm c_k of the coarse tensor */
+    double eps_left;   /* discarded eigenvalue weight of E_L (eps_1) */
+    double eps_right;  /* same for E_R (eps_2); NaN when env_policy = 1 */
+    int32_t side;      /* 0: projector from E_L; 1: from E_R */
+    int32_t dprime;    /* D' = min(D_cut, D_h^2) */
+    int32_t sweeps;    /* largest Jacobi sweep count over the sectors */
+    int32_t status;    /* hotrg_status of the device part of the step */
+} hotrg_step_info;
+
+/* Result of one point. */
+typedef struct {
+    double lnz_per_site;   /* ln Z / N, N = 2^n_steps */
+    double ln_c0;          /* ln ||T0||_F */
+    double ln_trace;       /* ln sum_{x,y} T[x,x,y,y] of the final tensor */
+    double imp_ratio;      /* tTr(T_imp)/tTr(T) when an impurity ran, else 0 */
+    hotrg_step_info step[HOTRG_MAX_STEPS];
+    int32_t n_steps;
+    int32_t status;
+} hotrg_result;
+
+/* Observables of one point (§3.4). */
+typedef struct {
+    double lnz;   /* ln Z / N at (beta, Delta, h = h1 = 0) */
+    double f;     /* -lnz / beta */
+    double cv;    /* Eq. 3.17 by central difference in beta */
+    double m;     /* <cos theta> at h = hbar (impurity, Eq. 3.20) */
+    double m1;    /* <cos 2 theta> at h1 = hbar (impurity, Eq. 3.21) */
+    double chi;   /* dm/dh at hbar by central difference (Eq. 3.18) */
+    double chi1;  /* dm1/dh1 at hbar by central difference */
+    int32_t status;
+    int32_t pad;
+} hotrg_obs;
+
+/* Create a context whose device work goes to cuda_stream (a cudaStream_t,
+ * NULL for the legacy default stream).  workspace_bytes reserves device
+ * memory up front (0: grow on demand; growth never happens during stream
+ * capture -- a run that needs more than the reservation returns
+ * HOTRG_ENOMEM while capturing).  Errors: HOTRG_EINVAL (ctx NULL),
+ * HOTRG_ENOMEM, HOTRG_ECUDA. */
+hotrg_status hotrg_create(hotrg_ctx** ctx, size_t workspace_bytes, void* cuda_stream);
+
+/* Release the context and its workspace.  NULL is a no-op. */
+void hotrg_destroy(hotrg_ctx* ctx);
+
+/* Build the initial site tensor (Eq. 3.4 coefficients with the own Bessel
+ * series on the device; Eq. 3.15 / 3.20 / 3.21 field and impurity factors)
+ * into T_dev (device, D0^4 FP64, [l][r][u][d], D0 = 2 n_max + 1; for
+ * HOTRG_T_ISING D0 = 2) and the D0 bond labels into labels_dev (device,
+ * int32).  The tensor is NOT normalised.  Errors: HOTRG_EINVAL for
+ * beta <= 0, Delta outside [0,1], negative fields, n_max outside [0, 64],
+ * m_range outside [1, 200], null pointers; HOTRG_ECUDA on launch failure. */
+hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const hotrg_params* p, int32_t kind,
+                               double* T_dev, int32_t* labels_dev);
+
+/* One coarse-graining step (§2.4.1) of the normalised tensor T_in (device,
+ * [Dh][Dh][Dv][Dv] FP64) with horizontal labels q_h (device, Dh int32) and
+ * vertical labels q_v (device, Dv int32).  Writes the normalised coarse
+ * tensor, already relabelled for the other axis, to T_out (device,
+ * [Dv][Dv][D'][D'], D' = min(d_cut, Dh^2)); its new vertical labels to
+ * q_out (device, D' int32; the new horizontal labels are q_v); D' to
+ * *dprime (host).  info_dev (device, may be NULL) receives the step's
+ * scalars.  T_imp_in / T_imp_out (device, may both be NULL) co-update an
+ * impurity tensor with the pure tensor's projector and norm:
+ * T_imp' = [P^T(T_imp above T)P + P^T(T above T_imp)P] / (2 c_k).
+ * T_out must not alias T_in.  Errors: HOTRG_EINVAL (sizes < 1, Dh > 128,
+ * Dv > 128, null pointers), HOTRG_ENOMEM (workspace), HOTRG_ECUDA. */
+hotrg_status hotrg_step(hotrg_ctx* ctx, const hotrg_params* p,
+                        const double* T_in, const int32_t* q_h, const int32_t* q_v,
+                        int32_t Dh, int32_t Dv,
+                        double* T_out, int32_t* q_out, int32_t* dprime,
+                        hotrg_step_info* info_dev,
+                        const double* T_imp_in, double* T_imp_out);
+
+/* Run npoints independent points params[0..npoints) (host array) from the
+ * initial tensor to ln Z / N, writing out[0..npoints) (host).  With
+ * imp_kind = HOTRG_T_IMP_M or HOTRG_T_IMP_M1 each point also carries that
+ * impurity tensor and reports imp_ratio; HOTRG_T_PURE runs the pure tensor
+ * only.  Returns the first non-OK point status (each out[i].status holds
+ * its own).  Synchronous. */
+hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
+                       int32_t imp_kind, hotrg_result* out);
+
+/* Observables of npoints points (§3.4): ln Z/N and f at zero field;
+ * C_V = beta^2 [l(beta+hb) - 2 l(beta) + l(beta-hb)] / hb^2 (Eq. 3.17);
+ * m = <cos theta> at h = hbar and m1 = <cos 2theta> at h1 = hbar from the
+ * impurity tensors (Eq. 3.19-3.21); chi, chi1 by central differences of m,
+ * m1 with step dh (Eq. 3.18).  The fields in params are ignored.
+ * Synchronous. */
+hotrg_status hotrg_observables(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
+                               double hb, double hbar, double dh, hotrg_obs* out);
+
+/* Text of the last error on this context ("" when none).  Valid until the
+ * next call on the same context. */
+const char* hotrg_last_error(hotrg_ctx* ctx);
+
+/* Library version string. */
+const char* hotrg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOTRG_H */

@@ -1,0 +1,28 @@
+// Contraction engine dispatch: every contraction of a step is C = A B^T with
+// K-contiguous FP64 operands and an FP64 result.  HOTRG_FP64 runs the SIMT
+// DFMA kernel; the tensor-core split forms live in hotrg_umma.cu.
+#include "internal.cuh"
+
+namespace hotrg {
+
+hotrg_status umma_gemm(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, bool coarse);
+size_t umma_workspace(int prec, int64_t M, int64_t N, int64_t K);
+
+hotrg_status gemm_engine(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                         int64_t ldb, double* C, int64_t ldc, bool coarse) {
+    if (M <= 0 || N <= 0) return HOTRG_OK;
+    if (prec == HOTRG_FP64) {
+        launch_gemm_tn_f64(M, N, K, A, lda, B, ldb, C, ldc, 1, 0, 0, 0, ctx->stream);
+        HOTRG_LAUNCH_CHECK(ctx, "gemm_tn_f64");
+        return HOTRG_OK;
+    }
+    return umma_gemm(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc, coarse);
+}
+
+size_t gemm_engine_workspace(int prec, int64_t M, int64_t N, int64_t K) {
+    if (prec == HOTRG_FP64) return 0;
+    return umma_workspace(prec, M, N, K);
+}
+
+}  // namespace hotrg

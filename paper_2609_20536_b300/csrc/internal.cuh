@@ -1,0 +1,112 @@
+// Internal declarations of libhotrg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hotrg.h"
+
+namespace hotrg {
+
+// Symmetry of the fused-leg labels: U(1) charge, Z2 parity, or none.
+enum SymMode : int { SYM_U1 = 0, SYM_Z2 = 1, SYM_NONE = 2 };
+
+struct Workspace {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t used = 0;
+    bool owned_growth_ok = true;
+};
+
+}  // namespace hotrg
+
+struct hotrg_ctx {
+    cudaStream_t stream = nullptr;
+    hotrg::Workspace ws;
+    std::string last_error;
+    int device = 0;
+    int sm_count = 148;
+    int smem_optin = 0;
+    bool tc_ok = false;  // sm_103a tensor-core path usable on this device
+};
+
+namespace hotrg {
+
+// ---- error helpers -------------------------------------------------------
+hotrg_status set_err(hotrg_ctx* ctx, hotrg_status st, const std::string& msg);
+
+#define HOTRG_CUDA_TRY(ctx, call)                                                           \
+    do {                                                                                    \
+        cudaError_t _e = (call);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            return ::hotrg::set_err((ctx), HOTRG_ECUDA,                                     \
+                                    std::string(#call) + ": " + cudaGetErrorString(_e));    \
+    } while (0)
+
+#define HOTRG_LAUNCH_CHECK(ctx, what)                                                       \
+    do {                                                                                    \
+        cudaError_t _e = cudaGetLastError();                                                \
+        if (_e != cudaSuccess)                                                              \
+            return ::hotrg::set_err((ctx), HOTRG_ECUDA,                                     \
+                                    std::string("launch ") + (what) + ": " +                \
+                                        cudaGetErrorString(_e));                            \
+    } while (0)
+
+// ---- workspace (bump allocator, 256-byte aligned) -------------------------
+hotrg_status ws_reserve(hotrg_ctx* ctx, size_t bytes);
+void* ws_alloc(hotrg_ctx* ctx, size_t bytes);  // returns nullptr when over capacity
+
+// ---- kernels: elementwise / tensor plumbing (hotrg_kernels.cu) ------------
+// Output-ordered permutation: out is contiguous with dims od[0..nd) (od[nd-1]
+// fastest); element (o_0..o_{nd-1}) is read from in[sum o_k * is[k]].
+void launch_permute(const double* in, double* out, int nd, const int64_t* od, const int64_t* is,
+                    cudaStream_t st);
+// C[b](M x N, ldc) = A[b](M x K, lda) * B[b](N x K, ldb)^T in FP64 (SIMT DFMA).
+void launch_gemm_tn_f64(int M, int N, int K, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, double* C, int64_t ldc, int batch, int64_t sA, int64_t sB,
+                        int64_t sC, cudaStream_t st);
+// Frobenius norm of x[0..n) into *norm (two-pass, deterministic); partial is a
+// scratch array of at least norm_partials() doubles.
+int norm_partials();
+void launch_norm(const double* x, int64_t n, double* partial, double* norm, cudaStream_t st);
+// x[i] *= 1 / *c  (c on the device)
+void launch_scale_inv(double* x, int64_t n, const double* c, cudaStream_t st);
+// *tr = sum_{x,y} T[x][x][y][y] for T [Dx][Dx][Dy][Dy]
+void launch_trace(const double* T, int Dx, int Dy, double* tr, cudaStream_t st);
+// Initial tensor (Eq. 3.4, 3.15, 3.20, 3.21) or the Ising tensor.
+void launch_init_tensor(const hotrg_params* p, int kind, double* T, int32_t* labels,
+                        double* scratch, cudaStream_t st);
+// Step bookkeeping: info->ln_c = log(*norm), lnz accumulation etc.
+void launch_step_scalars(const double* norm, hotrg_step_info* info, double* lnz_acc, double weight,
+                         cudaStream_t st);
+void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cudaStream_t st);
+
+// ---- eigensolver + truncation (hotrg_eig.cu) -------------------------------
+struct EigPlan {
+    int n;        // Dh^2 states
+    int Dh;
+    int dprime;
+    int sym;      // SymMode
+    int max_sweeps;
+    double tol;
+    double tie_rtol;
+    int env_policy;
+};
+size_t eig_workspace_bytes(int Dh);
+// E[0] = E_L, E[1] = E_R (E[1] may be null when env_policy == 1).  Writes P
+// ((Dh^2) x D' row-major), q_out (D'), and info->{eps_left, eps_right, side,
+// sweeps, status}.
+hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL, const double* ER,
+                          const int32_t* q_h, double* P, int32_t* q_out, hotrg_step_info* info,
+                          void* ws);
+
+// ---- contraction engines (FP64 SIMT; tensor-core split forms) -------------
+// C (M x N, ldc) = A (M x K, lda) * B (N x K, ldb)^T with FP64 in/out.
+hotrg_status gemm_engine(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda,
+                         const double* B, int64_t ldb, double* C, int64_t ldc, bool coarse);
+size_t gemm_engine_workspace(int prec, int64_t M, int64_t N, int64_t K);
+
+}  // namespace hotrg

@@ -1,0 +1,180 @@
+"""ctypes binding of libhotrg (argument marshalling only).
+
+Entry points keep the C names: hotrg_create, hotrg_destroy, hotrg_init_tensor,
+hotrg_step, hotrg_run, hotrg_observables, hotrg_last_error.  Device buffers
+are passed as integer addresses (e.g. ``torch.Tensor.data_ptr()``); host
+structs are the ctypes mirrors below.  Every numerical step runs in the CUDA
+library; there is no Python or CPU fallback, and importing this module fails
+when ``libhotrg.so`` is absent.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhotrg.so")
+
+MAX_STEPS = 64
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+FP64, SPLIT_BF16, TF32X3 = 0, 1, 2
+T_PURE, T_IMP_M, T_IMP_M1, T_ISING = 0, 1, 2, 3
+
+
+class HotrgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libhotrg status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("beta", ctypes.c_double), ("delta", ctypes.c_double),
+        ("h", ctypes.c_double), ("h1", ctypes.c_double),
+        ("n_max", ctypes.c_int32), ("d_cut", ctypes.c_int32), ("n_steps", ctypes.c_int32),
+        ("prec", ctypes.c_int32), ("env_policy", ctypes.c_int32), ("m_range", ctypes.c_int32),
+        ("eig_max_sweeps", ctypes.c_int32), ("tkind", ctypes.c_int32),
+        ("tie_rtol", ctypes.c_double), ("eig_tol", ctypes.c_double),
+    ]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [
+        ("ln_c", ctypes.c_double), ("eps_left", ctypes.c_double), ("eps_right", ctypes.c_double),
+        ("side", ctypes.c_int32), ("dprime", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("lnz_per_site", ctypes.c_double), ("ln_c0", ctypes.c_double), ("ln_trace", ctypes.c_double),
+        ("imp_ratio", ctypes.c_double), ("step", StepInfo * MAX_STEPS),
+        ("n_steps", ctypes.c_int32), ("status", ctypes.c_int32),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("lnz", ctypes.c_double), ("f", ctypes.c_double), ("cv", ctypes.c_double),
+        ("m", ctypes.c_double), ("m1", ctypes.c_double), ("chi", ctypes.c_double),
+        ("chi1", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhotrg.so not built ({LIB_PATH}); run paper_2609_20536_b300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.hotrg_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, vp]
+    lib.hotrg_create.restype = ctypes.c_int
+    lib.hotrg_destroy.argtypes = [vp]
+    lib.hotrg_destroy.restype = None
+    lib.hotrg_last_error.argtypes = [vp]
+    lib.hotrg_last_error.restype = ctypes.c_char_p
+    lib.hotrg_version.argtypes = []
+    lib.hotrg_version.restype = ctypes.c_char_p
+    lib.hotrg_init_tensor.argtypes = [vp, ctypes.POINTER(Params), i32, vp, vp]
+    lib.hotrg_init_tensor.restype = ctypes.c_int
+    lib.hotrg_step.argtypes = [vp, ctypes.POINTER(Params), vp, vp, vp, i32, i32, vp, vp,
+                               ctypes.POINTER(i32), vp, vp, vp]
+    lib.hotrg_step.restype = ctypes.c_int
+    lib.hotrg_run.argtypes = [vp, ctypes.POINTER(Params), i32, i32, ctypes.POINTER(Result)]
+    lib.hotrg_run.restype = ctypes.c_int
+    lib.hotrg_observables.argtypes = [vp, ctypes.POINTER(Params), i32, f64, f64, f64, ctypes.POINTER(Obs)]
+    lib.hotrg_observables.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def params(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, prec=FP64, env_policy=0, m_range=50,
+           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0):
+    return Params(beta, delta, h, h1, n_max, d_cut, n_steps, prec, env_policy, m_range,
+                  eig_max_sweeps, tkind, tie_rtol, eig_tol)
+
+
+def hotrg_create(workspace_bytes=0, stream=0):
+    h = ctypes.c_void_p()
+    st = lib.hotrg_create(ctypes.byref(h), workspace_bytes, ctypes.c_void_p(stream or None))
+    if st != OK:
+        raise HotrgError(st, "hotrg_create failed")
+    return h
+
+
+def hotrg_destroy(ctx):
+    lib.hotrg_destroy(ctx)
+
+
+def hotrg_last_error(ctx):
+    return lib.hotrg_last_error(ctx).decode()
+
+
+def _check(ctx, st):
+    if st != OK:
+        raise HotrgError(st, hotrg_last_error(ctx))
+    return st
+
+
+def hotrg_init_tensor(ctx, p, kind, T_ptr, labels_ptr):
+    return _check(ctx, lib.hotrg_init_tensor(ctx, ctypes.byref(p), kind, ctypes.c_void_p(T_ptr),
+                                             ctypes.c_void_p(labels_ptr)))
+
+
+def hotrg_step(ctx, p, T_in, q_h, q_v, Dh, Dv, T_out, q_out, info_dev=0, T_imp_in=0, T_imp_out=0):
+    dp = ctypes.c_int32(0)
+    _check(ctx, lib.hotrg_step(ctx, ctypes.byref(p), ctypes.c_void_p(T_in), ctypes.c_void_p(q_h),
+                               ctypes.c_void_p(q_v), Dh, Dv, ctypes.c_void_p(T_out), ctypes.c_void_p(q_out),
+                               ctypes.byref(dp), ctypes.c_void_p(info_dev or None),
+                               ctypes.c_void_p(T_imp_in or None), ctypes.c_void_p(T_imp_out or None)))
+    return dp.value
+
+
+def hotrg_run(ctx, plist, imp_kind=T_PURE, check=True):
+    n = len(plist)
+    arr = (Params * n)(*plist)
+    out = (Result * n)()
+    st = lib.hotrg_run(ctx, arr, n, imp_kind, out)
+    if check:
+        _check(ctx, st)
+    return list(out)
+
+
+def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
+    n = len(plist)
+    arr = (Params * n)(*plist)
+    out = (Obs * n)()
+    _check(ctx, lib.hotrg_observables(ctx, arr, n, hb, hbar, dh, out))
+    return list(out)
+
+
+class Context:
+    """Owns one hotrg_ctx bound to a CUDA stream (0: legacy default)."""
+
+    def __init__(self, workspace_bytes=0, stream=0):
+        self.handle = hotrg_create(workspace_bytes, stream)
+
+    def close(self):
+        if self.handle:
+            hotrg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, plist, imp_kind=T_PURE):
+        return hotrg_run(self.handle, plist, imp_kind)
+
+    def observables(self, plist, hb=1e-3, hbar=0.01, dh=1e-3):
+        return hotrg_observables(self.handle, plist, hb, hbar, dh)
