@@ -28,10 +28,15 @@
  *   - Precision forms: HOTRG_FP64 computes every contraction with FP64
  *     fused multiply-adds.  HOTRG_SPLIT_BF16 computes the environment and
  *     coarse contractions on the tensor cores from fixed-point BF16 slices
- *     of the FP64 operands (exact FP32 accumulation of slice products,
- *     FP64 recombination), keeping the eigensolve, normalisation and ln Z
- *     in FP64.  HOTRG_3XTF32 is the three-product TF32 split with FP32
- *     accumulation.
+ *     of the FP64 operands: per-row power-of-two scaling, balanced 8-bit
+ *     digits, 5 slices (39 bits, 15 slice products) for the coarse
+ *     contraction and 4 slices (31 bits, 10 products) for the environments.
+ *     Slice products accumulate exactly in FP32 over chunks of 512 and are
+ *     carried across chunks in double-float registers.  The environment
+ *     eigensolve (FP32 subspace iteration refined by an FP64 Rayleigh-Ritz
+ *     step on large blocks, FP64 Jacobi on small ones), normalisation and
+ *     ln Z stay FP64.  HOTRG_SPLIT_BF16_FAST uses 3 slices everywhere (23
+ *     bits, the FP32 accuracy class of a 3xTF32 split).
  */
 #ifndef HOTRG_H
 #define HOTRG_H
@@ -57,7 +62,7 @@ typedef enum {
     HOTRG_ENOTSUP = -6   /* form not available in this build / on this device */
 } hotrg_status;
 
-typedef enum { HOTRG_FP64 = 0, HOTRG_SPLIT_BF16 = 1, HOTRG_3XTF32 = 2 } hotrg_prec;
+typedef enum { HOTRG_FP64 = 0, HOTRG_SPLIT_BF16 = 1, HOTRG_SPLIT_BF16_FAST = 2 } hotrg_prec;
 
 typedef enum {
     HOTRG_T_PURE = 0,   /* Eq. 3.15: sqrt(a_l a_r a_u a_d) * sum_j I_{Q+2j}(bh) I_j(bh1) */
@@ -176,6 +181,17 @@ hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoin
  * Synchronous. */
 hotrg_status hotrg_observables(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
                                double hb, double hbar, double dh, hotrg_obs* out);
+
+/* Verification entry point for the contraction engine of a precision
+ * form: C = A B^T with A (device, M x K FP64, row stride lda), B (device,
+ * N x K FP64, row stride ldb), C (device, M x N FP64, row stride ldc).
+ * Every contraction of hotrg_step goes through this engine (the split forms
+ * with their coarse-contraction slice count).  Asynchronous.  Errors:
+ * HOTRG_EINVAL (sizes < 1, K > 16384, strides < K or < N, null pointers),
+ * HOTRG_ENOTSUP (split form without sm_103), HOTRG_ENOMEM, HOTRG_ECUDA. */
+hotrg_status hotrg_contract(hotrg_ctx* ctx, int32_t prec, int32_t M, int32_t N, int32_t K,
+                            const double* A, int64_t lda, const double* B, int64_t ldb,
+                            double* C, int64_t ldc);
 
 /* Text of the last error on this context ("" when none).  Valid until the
  * next call on the same context. */

@@ -105,7 +105,14 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
     const size_t d5 = Dp * Dh * Dh * Dv * Dv;
     b += a256(d4 * 8) * 2 + a256(d5 * 8) * 2 + a256(Dp * Dp * Dv * Dv * 8) * (imp ? 2 : 1);
     b += a256(norm_partials() * 8) + a256(64) * 4;
-    b += gemm_engine_workspace(p->prec, (int64_t)Dp * Dh * Dv, hv, hv);
+    const int64_t shapes[5][3] = {{(int64_t)hv, (int64_t)hv, (int64_t)hv},
+                                  {(int64_t)n, (int64_t)n, (int64_t)Dv * Dv},
+                                  {(int64_t)Dp * Dh, (int64_t)Dh * Dv * Dv, Dh},
+                                  {(int64_t)Dp * Dh * Dv, (int64_t)hv, (int64_t)hv},
+                                  {(int64_t)Dp * Dv * Dv, (int64_t)Dp, (int64_t)n}};
+    size_t g = 0;
+    for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
+    b += g;
     return b;
 }
 
@@ -251,6 +258,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     plan.tol = p->eig_tol > 0 ? p->eig_tol : 1e-15;
     plan.tie_rtol = p->tie_rtol > 0 ? p->tie_rtol : 1e-12;
     plan.env_policy = p->env_policy;
+    plan.exact = prec == HOTRG_FP64;
     if ((s = eig_truncate(ctx, plan, EL, p->env_policy == 0 ? ER : nullptr, q_h, P, q_out, info, eigws)) !=
         HOTRG_OK)
         return s;
@@ -375,6 +383,8 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
     HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(out->step, infos, sizeof(hotrg_step_info) * p->n_steps,
                                         cudaMemcpyDeviceToHost, st));
     HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (p->prec != HOTRG_FP64)
+        if ((s = umma_check_status(ctx)) != HOTRG_OK) { out->status = s; return s; }
     out->lnz_per_site = h.lnz;
     out->ln_c0 = h.ln_c0;
     out->ln_trace = h.ln_tr;
@@ -484,6 +494,22 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, const hotrg_params* p, const double* T_i
     s = do_step(ctx, p, T_in, q_h, q_v, Dh, Dv, T_out, q_out, &dp, info_dev, T_imp_in, T_imp_out, nullptr, 0.0);
     *dprime = dp;
     return s;
+}
+
+hotrg_status hotrg_contract(hotrg_ctx* ctx, int32_t prec, int32_t M, int32_t N, int32_t K, const double* A,
+                            int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc) {
+    if (!ctx) return HOTRG_EINVAL;
+    ctx->last_error.clear();
+    if (!A || !B || !C) return set_err(ctx, HOTRG_EINVAL, "null pointer argument");
+    if (M < 1 || N < 1 || K < 1 || K > 16384 || lda < K || ldb < K || ldc < N)
+        return set_err(ctx, HOTRG_EINVAL, "bad sizes or strides");
+    if (prec < HOTRG_FP64 || prec > HOTRG_SPLIT_BF16_FAST) return set_err(ctx, HOTRG_EINVAL, "unknown precision form");
+    if (prec != HOTRG_FP64 && !ctx->tc_ok) return set_err(ctx, HOTRG_ENOTSUP, "tensor-core forms need sm_103");
+    hotrg_status s = ws_reserve(ctx, gemm_engine_workspace(prec, M, N, K) + 4096);
+    if (s != HOTRG_OK) return s;
+    if (prec == HOTRG_FP64) return gemm_engine(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc, true);
+    if ((s = umma_contract(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc)) != HOTRG_OK) return s;
+    return umma_check_status(ctx);
 }
 
 hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints, int32_t imp_kind,

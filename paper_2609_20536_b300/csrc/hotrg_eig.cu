@@ -1,53 +1,79 @@
-// Truncation of one HOTRG step on the device (§2.4.1): per-sector FP64 Jacobi
-// eigensolve of the environments E_L / E_R, the cut-cluster selection of the
+// Truncation of one HOTRG step on the device (§2.4.1): eigenpairs of the
+// environments E_L / E_R per symmetry sector, the cut-cluster selection of the
 // top D' eigenpairs, the eps_1 / eps_2 side rule and the projector P.
 //
 // Block structure (§2.3.1: conserved quantum numbers make the decomposition
 // block-sparse): the fused state (a, b) of two horizontal legs carries the key
 // q_h[a] + q_h[b] (U(1) charge), its parity (Z2), or 0 (no symmetry); E is
-// block diagonal in the key and each block is diagonalised on its own.
+// block diagonal in the key and each block is solved on its own.
 //
-// Selection rule (the thesis leaves ties unstated): sort all eigenvalues
-// descending; those within tie_rtol * lambda_max of the D'-th largest form the
-// cut cluster, filled in order of |key| ascending, key descending, lambda
-// descending, slot ascending.  eps = sum of the discarded eigenvalues.  The
-// right environment's projector is used only when eps_R < eps_L (1 - 1e-12).
+// Two eigensolvers:
+//  * exact: cyclic parallel Jacobi in FP64 on the whole block (all m
+//    eigenpairs).  Used for every block of the FP64 form and for blocks of at
+//    most small_thr states in the split forms.
+//  * subspace: for larger blocks of the split forms, b <= m columns of FP32
+//    block subspace iteration (CGS2 orthonormalisation) followed by one FP64
+//    Rayleigh-Ritz step (FP64 CGS2, Y = E_q Q on many CTAs, Jacobi on the
+//    b x b projection).  Eigenvalues come out FP64-accurate; the weight of
+//    the b..m-1 eigenvalues that are not listed is Tr(E_q) - sum of the
+//    listed ones.  If a block's smallest listed eigenvalue reaches the cut,
+//    b was too small and the step reports HOTRG_ENOCONV.
+//
+// Selection rule (the thesis leaves ties unstated): sort all listed
+// eigenvalues descending; those within tie_rtol * lambda_max of the D'-th
+// largest form the cut cluster, filled in order of |key| ascending, key
+// descending, lambda descending, slot ascending.  eps = weight of everything
+// not kept.  The right environment's projector is used only when
+// eps_R < eps_L (1 - 1e-12).
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "internal.cuh"
 
 namespace hotrg {
 
-constexpr int MAX_N = 16384;        // Dh <= 128
+constexpr int MAX_N = 16384;  // Dh <= 128
 constexpr int SORT_THREADS = 1024;
 constexpr int JAC_THREADS = 512;
-constexpr int JAC_SMEM_M = 96;      // sectors up to this size run from shared memory
+constexpr int JAC_SMEM_M = 96;  // blocks up to this size run from shared memory
 constexpr int JAC_MAX_PAIRS = MAX_N / 2;
-// rotation parameters: 2 doubles + 2 ints per pair
-constexpr size_t JAC_PAIR_BYTES = 24;
+constexpr size_t JAC_PAIR_BYTES = 24;  // rotation parameters: 2 doubles + 2 ints per pair
 constexpr size_t JAC_SMEM_MAT = 2 * JAC_SMEM_M * JAC_SMEM_M * sizeof(double);
 constexpr size_t JAC_SMEM_BYTES =
     (JAC_SMEM_MAT + (JAC_SMEM_M / 2) * JAC_PAIR_BYTES) > (JAC_MAX_PAIRS * JAC_PAIR_BYTES)
         ? (JAC_SMEM_MAT + (JAC_SMEM_M / 2) * JAC_PAIR_BYTES)
         : (JAC_MAX_PAIRS * JAC_PAIR_BYTES);
+constexpr int BCAP_MAX = 112;  // largest subspace width (Rayleigh-Ritz block in shared memory)
+constexpr int SUB_THREADS = 512;
+constexpr int SUB_ITERS = 12;
+constexpr size_t RR_SMEM_BYTES = 2 * BCAP_MAX * BCAP_MAX * sizeof(double) + (BCAP_MAX / 2) * JAC_PAIR_BYTES + 1024;
+constexpr int GB_ROWS = 32;  // rows of E_q per CTA in the FP64 product
 
 struct EigWs {
-    // sector structure (shared by both sides)
-    int32_t* members;   // [n] state indices grouped by key
-    int32_t* sec_start; // [n + 1]
-    int32_t* sec_key;   // [n]
-    int64_t* sec_off;   // [n] offset of the sector's m x m block
-    int32_t* nsec;      // [1]
-    int32_t* slot_sec;  // [n] sector of each slot (slot = position in members)
+    // block structure (shared by both sides)
+    int32_t* members;    // [n] state indices grouped by key (ascending within a key)
+    int32_t* sec_start;  // [n + 1] start of each block in members
+    int32_t* sec_key;    // [n]
+    int64_t* sec_aoff;   // [n] offset of the block's m x m region
+    int32_t* sec_b;      // [n] listed eigenpairs of the block
+    int32_t* sec_cstart; // [n + 1] first candidate slot of the block
+    int32_t* nsec;       // [1]
+    int32_t* ncand;      // [1]
+    int32_t* cand_sec;   // [n] block of each candidate slot
     // per side
-    double* A[2];       // packed m x m blocks (working copy of E_q, then eigenvalues on the diagonal)
-    double* V[2];       // packed eigenvector blocks, V[i][j]: component i of eigenvector j
-    double* lam[2];     // [n] eigenvalue of each slot
-    int32_t* kept[2];   // [D'] kept slots in kept order
-    double* eps[2];     // [1]
-    int32_t* sweeps;    // [2]
-    int32_t* status;    // [1]
+    double* A[2];   // m x m regions: FP64 Jacobi work, or the FP32 copy of E_q
+    double* V[2];   // eigenvectors of the block, m x b (ld b), at sec_aoff
+    double* S1[2];  // FP32 Q of the subspace iteration
+    double* S2[2];  // FP32 Y, then FP64 Q
+    double* S3[2];  // FP64 E_q (packed)
+    double* S4[2];  // FP64 Y = E_q Q
+    double* lam[2];   // [n] eigenvalue of each candidate slot
+    double* rest[2];  // [n] unlisted weight of each block
+    int32_t* kept[2]; // [D'] kept slots
+    double* eps[2];   // [1]
+    int32_t* sweeps;  // [2]
+    int32_t* status;  // [1]
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -55,8 +81,8 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t eig_workspace_bytes(int Dh) {
     const size_t n = (size_t)Dh * Dh;
     size_t b = 0;
-    b += align256(n * 4) * 4 + align256((n + 1) * 4) + align256(n * 8) + align256(64);
-    for (int s = 0; s < 2; ++s) b += align256(n * n * 8) * 2 + align256(n * 8) + align256(n * 4) + align256(64);
+    b += align256(n * 4) * 5 + align256((n + 1) * 4) * 2 + align256(n * 8) + align256(64) * 2;
+    for (int s = 0; s < 2; ++s) b += align256(n * n * 8) * 6 + align256(n * 8) * 2 + align256(n * 4) + align256(64);
     b += align256(64) * 2;
     return b;
 }
@@ -72,13 +98,21 @@ static EigWs carve(void* base, int n) {
     w.members = (int32_t*)take((size_t)n * 4);
     w.sec_start = (int32_t*)take((size_t)(n + 1) * 4);
     w.sec_key = (int32_t*)take((size_t)n * 4);
-    w.sec_off = (int64_t*)take((size_t)n * 8);
+    w.sec_aoff = (int64_t*)take((size_t)n * 8);
+    w.sec_b = (int32_t*)take((size_t)n * 4);
+    w.sec_cstart = (int32_t*)take((size_t)(n + 1) * 4);
     w.nsec = (int32_t*)take(64);
-    w.slot_sec = (int32_t*)take((size_t)n * 4);
+    w.ncand = (int32_t*)take(64);
+    w.cand_sec = (int32_t*)take((size_t)n * 4);
     for (int s = 0; s < 2; ++s) {
         w.A[s] = (double*)take((size_t)n * n * 8);
         w.V[s] = (double*)take((size_t)n * n * 8);
+        w.S1[s] = (double*)take((size_t)n * n * 8);
+        w.S2[s] = (double*)take((size_t)n * n * 8);
+        w.S3[s] = (double*)take((size_t)n * n * 8);
+        w.S4[s] = (double*)take((size_t)n * n * 8);
         w.lam[s] = (double*)take((size_t)n * 8);
+        w.rest[s] = (double*)take((size_t)n * 8);
         w.kept[s] = (int32_t*)take((size_t)n * 4);
         w.eps[s] = (double*)take(64);
     }
@@ -88,7 +122,7 @@ static EigWs carve(void* base, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// Sector discovery: sort (key, state) pairs, then segment by key.
+// Block discovery: sort (key, state) pairs, then segment by key.
 // ---------------------------------------------------------------------------
 __device__ void bitonic_sort_u64(uint64_t* a, int npow2) {
     for (int k = 2; k <= npow2; k <<= 1) {
@@ -109,7 +143,8 @@ __device__ void bitonic_sort_u64(uint64_t* a, int npow2) {
     }
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) sectors_kernel(const int32_t* q_h, int Dh, int sym, EigWs w) {
+__global__ void __launch_bounds__(SORT_THREADS) sectors_kernel(const int32_t* q_h, int Dh, int sym, int small_thr,
+                                                                int bcap, EigWs w) {
     extern __shared__ uint64_t su[];
     const int n = Dh * Dh;
     int npow2 = 1;
@@ -130,25 +165,32 @@ __global__ void __launch_bounds__(SORT_THREADS) sectors_kernel(const int32_t* q_
     __syncthreads();
     if (threadIdx.x == 0) {
         int ns = 0;
-        int64_t off = 0;
         int prev_key = 0;
         for (int i = 0; i < n; ++i) {
             const int key = (int)(su[i] >> 32) - (1 << 30);
             if (i == 0 || key != prev_key) {
-                if (ns > 0) {
-                    const int m = i - w.sec_start[ns - 1];
-                    off += (int64_t)m * m;
-                }
                 w.sec_start[ns] = i;
                 w.sec_key[ns] = key;
-                w.sec_off[ns] = off;
                 ++ns;
                 prev_key = key;
             }
-            w.slot_sec[i] = ns - 1;
         }
         w.sec_start[ns] = n;
+        int64_t off = 0;
+        int cs = 0;
+        for (int s = 0; s < ns; ++s) {
+            const int m = w.sec_start[s + 1] - w.sec_start[s];
+            const int b = m <= small_thr ? m : min(m, bcap);
+            w.sec_aoff[s] = off;
+            w.sec_b[s] = b;
+            w.sec_cstart[s] = cs;
+            for (int j = 0; j < b; ++j) w.cand_sec[cs + j] = s;
+            off += (int64_t)m * m;
+            cs += b;
+        }
+        w.sec_cstart[ns] = cs;
         *w.nsec = ns;
+        *w.ncand = cs;
         w.sweeps[0] = 0;
         w.sweeps[1] = 0;
         *w.status = HOTRG_OK;
@@ -286,8 +328,9 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_sectors_kernel(const doubl
     for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
         const int start = w.sec_start[sct];
         const int m = w.sec_start[sct + 1] - start;
-        double* Ag = w.A[side] + w.sec_off[sct];
-        double* Vg = w.V[side] + w.sec_off[sct];
+        if (w.sec_b[sct] != m) continue;  // solved by the subspace path
+        double* Ag = w.A[side] + w.sec_aoff[sct];
+        double* Vg = w.V[side] + w.sec_aoff[sct];
         const bool in_smem = m <= JAC_SMEM_M;
         double* A = in_smem ? sm : Ag;
         double* V = in_smem ? sm + JAC_SMEM_M * JAC_SMEM_M : Vg;
@@ -302,10 +345,296 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_sectors_kernel(const doubl
         }
         __syncthreads();
         const int sw = jacobi_block(A, V, m, max_sweeps, tol, rc, rs, rp, rq, red, &s_rot);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) w.lam[side][start + i] = A[i * m + i];
+        const int cs = w.sec_cstart[sct];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) w.lam[side][cs + i] = A[i * m + i];
         if (in_smem)
             for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) Vg[idx] = V[idx];
         if (threadIdx.x == 0) {
+            w.rest[side][sct] = 0.0;
+            if (sw < 0)
+                atomicExch(w.status, (int)HOTRG_ENOCONV);
+            else
+                atomicMax(&w.sweeps[side], sw);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Subspace path, FP32 part: b columns of block subspace iteration.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
+    uint32_t x = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 12;
+    x *= 0x297A2D39u;
+    x ^= x >> 15;
+    return (float)(x & 0xffffff) / 8388608.0f - 1.0f;  // [-1, 1)
+}
+
+// Orthonormalise the b columns of Y (m x b, ld b) in place: classical
+// Gram-Schmidt applied twice per column.  A column whose remainder falls below
+// dep_tol of its norm before orthogonalisation is numerically dependent on the
+// previous ones (E_q is often rank deficient); it is replaced by a fresh
+// pseudo-random vector (salted by the caller) and orthogonalised again, since
+// normalising a round-off remainder would destroy orthogonality.
+template <typename T>
+__device__ void cgs2(T* Y, int m, int b, T* r, double* red, uint32_t salt, double dep_tol) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = 0; j < b; ++j) {
+        bool done = false;
+        for (int attempt = 0; attempt < 4 && !done; ++attempt) {
+            if (attempt > 0) {
+                for (int t = threadIdx.x; t < m; t += blockDim.x)
+                    Y[(int64_t)t * b + j] = (T)hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)j);
+                __syncthreads();
+            }
+            double n0 = 0.0;
+            for (int t = threadIdx.x; t < m; t += blockDim.x)
+                n0 += (double)Y[(int64_t)t * b + j] * (double)Y[(int64_t)t * b + j];
+            n0 = block_reduce_sum(n0, red);
+            for (int pass = 0; pass < 2 && j > 0; ++pass) {
+                for (int i = warp; i < j; i += nw) {
+                    T acc = 0;
+                    for (int t = lane; t < m; t += 32) acc += Y[(int64_t)t * b + i] * Y[(int64_t)t * b + j];
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) r[i] = acc;
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                    T acc = 0;
+                    for (int i = 0; i < j; ++i) acc += r[i] * Y[(int64_t)t * b + i];
+                    Y[(int64_t)t * b + j] -= acc;
+                }
+                __syncthreads();
+            }
+            double nrm = 0.0;
+            for (int t = threadIdx.x; t < m; t += blockDim.x)
+                nrm += (double)Y[(int64_t)t * b + j] * (double)Y[(int64_t)t * b + j];
+            nrm = block_reduce_sum(nrm, red);
+            if (nrm > dep_tol * dep_tol * n0 && nrm > 1e-280) {
+                const T inv = (T)(1.0 / sqrt(nrm));
+                for (int t = threadIdx.x; t < m; t += blockDim.x) Y[(int64_t)t * b + j] *= inv;
+                done = true;
+            }
+            __syncthreads();
+        }
+        if (!done) {  // b exceeds the dimension that can be spanned: leave a zero column
+            for (int t = threadIdx.x; t < m; t += blockDim.x) Y[(int64_t)t * b + j] = (T)0;
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double* EL, const double* ER, int n,
+                                                                    int iters, EigWs w) {
+    __shared__ float Es[32][65];
+    __shared__ float Qs[64][BCAP_MAX + 1];
+    __shared__ float rbuf[BCAP_MAX];
+    __shared__ double red[40];
+    const int side = blockIdx.y;
+    const double* E = side == 0 ? EL : ER;
+    const int nsec = *w.nsec;
+    for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
+        const int start = w.sec_start[sct];
+        const int m = w.sec_start[sct + 1] - start;
+        const int b = w.sec_b[sct];
+        if (b == m) continue;
+        const int64_t aoff = w.sec_aoff[sct];
+        float* Ef = (float*)(w.A[side] + aoff);
+        float* Q = (float*)(w.S1[side] + aoff);
+        float* Y = (float*)(w.S2[side] + aoff);
+        double* E64 = w.S3[side] + aoff;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
+            const int i = (int)(idx / m), j = (int)(idx % m);
+            const double v = E[(int64_t)w.members[start + i] * n + w.members[start + j]];
+            E64[idx] = v;
+            Ef[idx] = (float)v;
+        }
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x)
+            Q[idx] = hash_unit((uint32_t)(idx / b), (uint32_t)(idx % b));
+        __syncthreads();
+        cgs2<float>(Q, m, b, rbuf, red, 1u, 1e-3);
+        for (int it = 0; it < iters; ++it) {
+            // Y = Ef Q (m x b), tiled: 32 rows of Ef x 64 k per pass
+            for (int r0 = 0; r0 < m; r0 += 32) {
+                float acc[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] = 0.f;
+                for (int k0 = 0; k0 < m; k0 += 64) {
+                    for (int idx = threadIdx.x; idx < 32 * 64; idx += blockDim.x) {
+                        const int i = idx / 64, k = idx % 64;
+                        Es[i][k] = (r0 + i < m && k0 + k < m) ? Ef[(int64_t)(r0 + i) * m + k0 + k] : 0.f;
+                    }
+                    for (int idx = threadIdx.x; idx < 64 * b; idx += blockDim.x) {
+                        const int k = idx / b, j = idx % b;
+                        Qs[k][j] = (k0 + k < m) ? Q[(int64_t)(k0 + k) * b + j] : 0.f;
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int o = threadIdx.x + u * SUB_THREADS;  // output index inside the 32 x b tile
+                        if (o < 32 * b) {
+                            const int i = o / b, j = o % b;
+                            float a = acc[u];
+                            for (int k = 0; k < 64; ++k) a = fmaf(Es[i][k], Qs[k][j], a);
+                            acc[u] = a;
+                        }
+                    }
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int o = threadIdx.x + u * SUB_THREADS;
+                    if (o < 32 * b) {
+                        const int i = o / b, j = o % b;
+                        if (r0 + i < m) Y[(int64_t)(r0 + i) * b + j] = acc[u];
+                    }
+                }
+                __syncthreads();
+            }
+            cgs2<float>(Y, m, b, rbuf, red, 2u + 4u * (uint32_t)it, 1e-3);
+            float* t = Q;  // the orthonormal Y becomes the next Q
+            Q = Y;
+            Y = t;
+        }
+        // leave the final basis in S1
+        if (Q != (float*)(w.S1[side] + aoff)) {
+            float* dst = (float*)(w.S1[side] + aoff);
+            for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) dst[idx] = Q[idx];
+        }
+        __syncthreads();
+    }
+}
+
+// FP64 basis: Q64 = CGS2(double(Q32)), in S2.
+__global__ void __launch_bounds__(SUB_THREADS) rr_prep_kernel(EigWs w) {
+    __shared__ double rbuf[BCAP_MAX];
+    __shared__ double red[40];
+    const int side = blockIdx.y;
+    const int nsec = *w.nsec;
+    for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
+        const int m = w.sec_start[sct + 1] - w.sec_start[sct];
+        const int b = w.sec_b[sct];
+        if (b == m) continue;
+        const int64_t aoff = w.sec_aoff[sct];
+        const float* Q32 = (const float*)(w.S1[side] + aoff);
+        double* Q = w.S2[side] + aoff;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) Q[idx] = (double)Q32[idx];
+        __syncthreads();
+        cgs2<double>(Q, m, b, rbuf, red, 100003u, 1e-8);
+    }
+}
+
+// Y = E_q Q (FP64) for all subspace blocks: CTA (row tile, block); 32 rows x b columns.
+__global__ void __launch_bounds__(256) rr_product_kernel(EigWs w) {
+    __shared__ double Es[GB_ROWS][33];
+    __shared__ double Qs[32][BCAP_MAX + 1];
+    const int side = blockIdx.z;
+    const int nsec = *w.nsec;
+    for (int sct = blockIdx.y; sct < nsec; sct += gridDim.y) {
+        const int m = w.sec_start[sct + 1] - w.sec_start[sct];
+        const int b = w.sec_b[sct];
+        if (b == m) continue;
+        const int64_t aoff = w.sec_aoff[sct];
+        const double* E = w.S3[side] + aoff;
+        const double* Q = w.S2[side] + aoff;
+        double* Y = w.S4[side] + aoff;
+        for (int r0 = blockIdx.x * GB_ROWS; r0 < m; r0 += gridDim.x * GB_ROWS) {
+            double acc[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+            for (int k0 = 0; k0 < m; k0 += 32) {
+                for (int idx = threadIdx.x; idx < GB_ROWS * 32; idx += blockDim.x) {
+                    const int i = idx / 32, k = idx % 32;
+                    Es[i][k] = (r0 + i < m && k0 + k < m) ? E[(int64_t)(r0 + i) * m + k0 + k] : 0.0;
+                }
+                for (int idx = threadIdx.x; idx < 32 * b; idx += blockDim.x) {
+                    const int k = idx / b, j = idx % b;
+                    Qs[k][j] = (k0 + k < m) ? Q[(int64_t)(k0 + k) * b + j] : 0.0;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int o = threadIdx.x + u * 256;
+                    if (o < GB_ROWS * b) {
+                        const int i = o / b, j = o % b;
+                        double a = acc[u];
+                        for (int k = 0; k < 32; ++k) a = fma(Es[i][k], Qs[k][j], a);
+                        acc[u] = a;
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int o = threadIdx.x + u * 256;
+                if (o < GB_ROWS * b) {
+                    const int i = o / b, j = o % b;
+                    if (r0 + i < m) Y[(int64_t)(r0 + i) * b + j] = acc[u];
+                }
+            }
+        }
+    }
+}
+
+// H = Q^T Y, Jacobi on H, V = Q W; eigenvalues and the unlisted weight.
+__global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, double tol, EigWs w) {
+    extern __shared__ double sm[];
+    __shared__ double red[40];
+    __shared__ int s_rot;
+    const int side = blockIdx.y;
+    const int nsec = *w.nsec;
+    for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
+        const int m = w.sec_start[sct + 1] - w.sec_start[sct];
+        const int b = w.sec_b[sct];
+        if (b == m) continue;
+        const int64_t aoff = w.sec_aoff[sct];
+        const double* Q = w.S2[side] + aoff;
+        const double* Y = w.S4[side] + aoff;
+        const double* E = w.S3[side] + aoff;
+        double* H = sm;
+        double* W = sm + BCAP_MAX * BCAP_MAX;
+        double* rc = sm + 2 * BCAP_MAX * BCAP_MAX;
+        double* rs = rc + BCAP_MAX / 2;
+        int* rp = (int*)(rs + BCAP_MAX / 2);
+        int* rq = rp + BCAP_MAX / 2;
+        // H = Q^T Y, symmetrised
+        for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+            const int i = idx / b, j = idx % b;
+            double a = 0.0;
+            for (int t = 0; t < m; ++t) a = fma(Q[(int64_t)t * b + i], Y[(int64_t)t * b + j], a);
+            H[idx] = a;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+            const int i = idx / b, j = idx % b;
+            if (i < j) {
+                const double s = 0.5 * (H[i * b + j] + H[j * b + i]);
+                H[i * b + j] = s;
+                H[j * b + i] = s;
+            }
+        }
+        __syncthreads();
+        const int sw = jacobi_block(H, W, b, max_sweeps, tol, rc, rs, rp, rq, red, &s_rot);
+        // Ritz vectors V = Q W (m x b)
+        double* V = w.V[side] + aoff;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) {
+            const int t = (int)(idx / b), j = (int)(idx % b);
+            double a = 0.0;
+            for (int i = 0; i < b; ++i) a = fma(Q[(int64_t)t * b + i], W[i * b + j], a);
+            V[idx] = a;
+        }
+        const int cs = w.sec_cstart[sct];
+        for (int j = threadIdx.x; j < b; j += blockDim.x) w.lam[side][cs + j] = H[j * b + j];
+        // unlisted weight: Tr(E_q) - sum of the listed eigenvalues
+        double tr = 0.0;
+        for (int t = threadIdx.x; t < m; t += blockDim.x) tr += E[(int64_t)t * m + t];
+        for (int j = threadIdx.x; j < b; j += blockDim.x) tr -= H[j * b + j];
+        tr = block_reduce_sum(tr, red);
+        if (threadIdx.x == 0) {
+            w.rest[side][sct] = tr > 0.0 ? tr : 0.0;
             if (sw < 0)
                 atomicExch(w.status, (int)HOTRG_ENOCONV);
             else
@@ -360,24 +689,30 @@ __device__ void bitonic_sort_idx(int* a, int npow2, const SelCmp& cmp) {
     }
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) select_kernel(int n, int dprime, double tie_rtol, EigWs w) {
+__global__ void __launch_bounds__(SORT_THREADS) select_kernel(int dprime, double tie_rtol, EigWs w) {
     extern __shared__ int si[];
     __shared__ double red[40];
     __shared__ int s_bounds[2];
     const int side = blockIdx.x;
     const double* lam = w.lam[side];
+    const int n = *w.ncand;
+    const int nsec = *w.nsec;
     int* slotkey = si + MAX_N;  // key per slot
     int npow2 = 1;
     while (npow2 < n) npow2 <<= 1;
     for (int i = threadIdx.x; i < npow2; i += blockDim.x) si[i] = i < n ? i : -1;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) slotkey[i] = w.sec_key[w.slot_sec[i]];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) slotkey[i] = w.sec_key[w.cand_sec[i]];
     __syncthreads();
     SelCmp cmp{lam, slotkey, 0};
     bitonic_sort_idx(si, npow2, cmp);
     int* kept = w.kept[side];
+    // weight of the eigenvalues no block listed
+    double unl = 0.0;
+    for (int s = threadIdx.x; s < nsec; s += blockDim.x) unl += w.rest[side][s];
+    unl = block_reduce_sum(unl, red);
     if (n <= dprime) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) kept[i] = si[i];
-        if (threadIdx.x == 0) *w.eps[side] = 0.0;
+        if (threadIdx.x == 0) *w.eps[side] = unl;
         return;
     }
     const double lmax = lam[si[0]];
@@ -395,6 +730,16 @@ __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int n, int dprime,
     const int n_above = s_bounds[0], n_end = s_bounds[1];
     const int need = dprime - n_above;
     const int ncl = n_end - n_above;
+    // a block whose smallest listed eigenvalue reaches the cut listed too few
+    for (int s = threadIdx.x; s < nsec; s += blockDim.x) {
+        const int m = w.sec_start[s + 1] - w.sec_start[s];
+        const int b = w.sec_b[s];
+        if (b < m) {
+            double lo = 1e300;
+            for (int j = 0; j < b; ++j) lo = fmin(lo, lam[w.sec_cstart[s] + j]);
+            if (lo >= lcut - tol) atomicExch(w.status, (int)HOTRG_ENOCONV);
+        }
+    }
     // sort the cluster by the tie rule in a separate power-of-two window
     int* cl = slotkey + MAX_N;  // MAX_N ints
     int cpow2 = 1;
@@ -420,25 +765,26 @@ __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int n, int dprime,
         s = t;
     }
     const double tot = block_reduce_sum(s, red);
-    if (threadIdx.x == 0) *w.eps[side] = tot;
+    if (threadIdx.x == 0) *w.eps[side] = tot + unl;
 }
 
 // ---------------------------------------------------------------------------
 // Side choice and projector P[(a,b)][j] (P must be zeroed beforehand).
 // ---------------------------------------------------------------------------
-__global__ void projector_kernel(int n, int dprime, int policy, EigWs w, double* P, int32_t* q_out,
+__global__ void projector_kernel(int dprime, int policy, EigWs w, double* P, int32_t* q_out,
                                  hotrg_step_info* info) {
     const double eL = *w.eps[0];
     const double eR = policy == 0 ? *w.eps[1] : nan("");
     const int side = (policy == 0 && eR < eL * (1.0 - 1e-12)) ? 1 : 0;
     const int j = blockIdx.x;
     const int slot = w.kept[side][j];
-    const int sct = w.slot_sec[slot];
+    const int sct = w.cand_sec[slot];
     const int start = w.sec_start[sct];
     const int m = w.sec_start[sct + 1] - start;
-    const int pos = slot - start;
-    const double* V = w.V[side] + w.sec_off[sct];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) P[(int64_t)w.members[start + i] * dprime + j] = V[i * m + pos];
+    const int b = w.sec_b[sct];
+    const int pos = slot - w.sec_cstart[sct];
+    const double* V = w.V[side] + w.sec_aoff[sct];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) P[(int64_t)w.members[start + i] * dprime + j] = V[(int64_t)i * b + pos];
     if (threadIdx.x == 0) q_out[j] = w.sec_key[sct];
     if (j == 0 && threadIdx.x == 0 && info) {
         info->eps_left = eL;
@@ -464,20 +810,60 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)JAC_SMEM_BYTES));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  MAX_N * 4 * 3));
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)RR_SMEM_BYTES));
         g_attr_done = true;
     }
     EigWs w = carve(ws, n);
-    sectors_kernel<<<1, SORT_THREADS, MAX_N * 8, st>>>(q_h, plan.Dh, plan.sym, w);
+    // listed width of large blocks in the split forms
+    int bcap;
+    if (plan.sym == SYM_NONE)
+        bcap = plan.dprime + 16;
+    else if (plan.sym == SYM_Z2)
+        bcap = plan.dprime / 2 + 24;
+    else
+        bcap = plan.dprime + 8 < 48 ? plan.dprime + 8 : 48;
+    if (bcap > BCAP_MAX) bcap = BCAP_MAX;
+    // tuning / diagnosis overrides: HOTRG_EIG_EXACT=1 forces FP64 Jacobi on every
+    // block, HOTRG_SUB_ITERS sets the FP32 subspace iterations
+    static int force_exact = -1, sub_iters = SUB_ITERS, thr_override = 0, bcap_override = 0;
+    if (force_exact < 0) {
+        const char* v = getenv("HOTRG_EIG_EXACT");
+        force_exact = (v && v[0] == '1') ? 1 : 0;
+        const char* it = getenv("HOTRG_SUB_ITERS");
+        if (it && atoi(it) > 0 && atoi(it) <= 200) sub_iters = atoi(it);
+        const char* th = getenv("HOTRG_SMALL_THR");
+        if (th && atoi(th) > 0) thr_override = atoi(th);
+        const char* bc = getenv("HOTRG_BCAP");
+        if (bc && atoi(bc) > 0 && atoi(bc) <= BCAP_MAX) bcap_override = atoi(bc);
+    }
+    if (bcap_override) bcap = bcap_override;
+    const bool exact = plan.exact || force_exact == 1;
+    int small_thr = exact ? n : (bcap > 48 ? bcap : 48);
+    if (!exact && thr_override) small_thr = thr_override;
+    sectors_kernel<<<1, SORT_THREADS, MAX_N * 8, st>>>(q_h, plan.Dh, plan.sym, small_thr, bcap, w);
     HOTRG_LAUNCH_CHECK(ctx, "sectors_kernel");
     const int sides = plan.env_policy == 0 ? 2 : 1;
-    int grid = n < 2 * ctx->sm_count ? n : 2 * ctx->sm_count;
+    const int grid = n < 2 * ctx->sm_count ? n : 2 * ctx->sm_count;
     jacobi_sectors_kernel<<<dim3(grid, sides), JAC_THREADS, JAC_SMEM_BYTES, st>>>(EL, ER, n, plan.max_sweeps,
                                                                                   plan.tol, w);
     HOTRG_LAUNCH_CHECK(ctx, "jacobi_sectors_kernel");
-    select_kernel<<<sides, SORT_THREADS, MAX_N * 4 * 3, st>>>(n, plan.dprime, plan.tie_rtol, w);
+    if (!exact) {
+        const int sgrid = n < ctx->sm_count ? n : ctx->sm_count;
+        subspace_fp32_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(EL, ER, n, sub_iters, w);
+        HOTRG_LAUNCH_CHECK(ctx, "subspace_fp32_kernel");
+        rr_prep_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(w);
+        HOTRG_LAUNCH_CHECK(ctx, "rr_prep_kernel");
+        const int tiles = (n + GB_ROWS - 1) / GB_ROWS;
+        rr_product_kernel<<<dim3(tiles < 64 ? tiles : 64, sgrid < 32 ? sgrid : 32, sides), 256, 0, st>>>(w);
+        HOTRG_LAUNCH_CHECK(ctx, "rr_product_kernel");
+        rr_finish_kernel<<<dim3(sgrid, sides), JAC_THREADS, RR_SMEM_BYTES, st>>>(plan.max_sweeps, plan.tol, w);
+        HOTRG_LAUNCH_CHECK(ctx, "rr_finish_kernel");
+    }
+    select_kernel<<<sides, SORT_THREADS, MAX_N * 4 * 3, st>>>(plan.dprime, plan.tie_rtol, w);
     HOTRG_LAUNCH_CHECK(ctx, "select_kernel");
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(P, 0, (size_t)n * plan.dprime * sizeof(double), st));
-    projector_kernel<<<plan.dprime, 128, 0, st>>>(n, plan.dprime, plan.env_policy, w, P, q_out, info);
+    projector_kernel<<<plan.dprime, 128, 0, st>>>(plan.dprime, plan.env_policy, w, P, q_out, info);
     HOTRG_LAUNCH_CHECK(ctx, "projector_kernel");
     return HOTRG_OK;
 }

@@ -17,7 +17,11 @@ hotrg_status gemm_engine(hotrg_ctx* ctx, int prec, int M, int N, int K, const do
         HOTRG_LAUNCH_CHECK(ctx, "gemm_tn_f64");
         return HOTRG_OK;
     }
-    return umma_gemm(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc, coarse);
+    // slice buffers live only until the (stream-ordered) GEMM has consumed them
+    const size_t mark = ctx->ws.used;
+    hotrg_status s = umma_gemm(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc, coarse);
+    ctx->ws.used = mark;
+    return s;
 }
 
 size_t gemm_engine_workspace(int prec, int64_t M, int64_t N, int64_t K) {

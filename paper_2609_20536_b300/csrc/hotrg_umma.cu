@@ -1,18 +1,668 @@
-// Tensor-core split-precision contraction engine (sm_103a).  Placeholder
-// until the tcgen05 kernels land: the split forms report HOTRG_ENOTSUP.
+// Split-precision contraction engine on the 5th-generation tensor cores
+// (tcgen05, sm_103a): C = A B^T for FP64 (or FP32-pair) operands, computed
+// from fixed-point BF16 slices whose products accumulate exactly.
+//
+// Slicing (per row of A and per row of B, i.e. per output row / column):
+//   e      = exponent with max_k |X_k| < 2^e (a power of two per row)
+//   F_k    = round(X_k 2^(T - e)), a signed integer, T = 7 + 8 (NS - 1) bits
+//   digits = NS balanced digits c_0 .. c_{NS-1}, |c_p| <= 128, F = sum c_p 2^(8(NS-1-p))
+//   slice p holds c_p 2^(-8p): at most 8 significant bits, exact in BF16.
+// The tensor cores accumulate in FP32 by truncation, so only sums that stay
+// exactly representable are safe.  Every slice product is an integer (times a
+// power of two) of magnitude <= 2^14.  Over a chunk of 512 values of k the
+// diagonal-0 sum (c_0 c_0', one product per k) and the diagonal-1 sum
+// (c_0 c_1' + c_1 c_0') stay <= 2^24 and are exact; diagonals p + q >= 2 sit
+// 2^-16 below the leading term and go to a third accumulator whose FP32
+// error is below 2^-28 of the result.  After each chunk the epilogue warps
+// fold the three TMEM accumulators into per-element double-float running
+// sums (error-free TwoSum), then hand TMEM back for the next chunk.  Pairs
+// with p + q > NS - 1 are dropped (2^-8NS below the leading term).  Result:
+//   C = (hi + lo) 2^(eA + eB - 14).
+//
+// The GEMM kernel: one CTA per 128 x 128 output tile.  Warp 0 issues TMA loads
+// (all NS slices of a 128 x 32 A tile and a 128 x 32 B tile per stage, 64-byte
+// swizzle), warp 1 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM),
+// warps 2..9 drain the accumulators per chunk.  Every mbarrier wait is
+// bounded; on timeout the kernel records HOTRG_ETIMEOUT in a device status
+// word, other CTAs see it and leave, and each CTA drains its own copies first.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+
 #include "internal.cuh"
 
 namespace hotrg {
 
-hotrg_status umma_gemm(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda, const double* B,
-                       int64_t ldb, double* C, int64_t ldc, bool coarse) {
-    (void)prec; (void)M; (void)N; (void)K; (void)A; (void)lda; (void)B; (void)ldb; (void)C; (void)ldc; (void)coarse;
-    return set_err(ctx, HOTRG_ENOTSUP, "split-precision engine not built");
+// ---------------------------------------------------------------------------
+// output / input element formats of the engine
+// ---------------------------------------------------------------------------
+enum ElemFmt : int { FMT_F64 = 0, FMT_F32PAIR = 1 };
+
+// Bits of the leading digit and the K extent of one exactly-accumulated chunk:
+// with |c| <= 128 every slice product is at most 2^14, so the diagonal-0 sum
+// (one product per k) and the diagonal-1 sum (two products per k) over 512
+// values of k stay within 2^24 and are exact in FP32.
+constexpr int SLICE_B1 = 7;
+constexpr int KCHUNK = 512;
+
+// ---------------------------------------------------------------------------
+// Slicing kernel: one warp per row.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int exp_f64(double v) {  // floor(log2 |v|) for normal v; -2000 for 0
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return -2000;  // zero or subnormal: treated as zero
+    return ex - 1023;
 }
 
+__device__ __forceinline__ int exp_f32(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int ex = (int)((b >> 23) & 0xff);
+    if (ex == 0) return -2000;
+    return ex - 127;
+}
+
+// round(|v| 2^sh) as an unsigned 64-bit integer, for |v| 2^sh < 2^62 (FP64 input)
+__device__ __forceinline__ uint64_t fixed_f64(double v, int sh) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;
+    const uint64_t mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int s = ex - 1075 + sh;  // value = mant 2^(ex - 1075), times 2^sh
+    if (s >= 0) return s >= 10 ? 0 : (mant << s);  // not reached for |v| 2^sh < 2^62
+    const int r = -s;
+    if (r >= 63) return 0;
+    return (mant + (1ull << (r - 1))) >> r;
+}
+
+__device__ __forceinline__ uint64_t fixed_f32(float v, int sh) {
+    const uint32_t b = __float_as_uint(v);
+    const int ex = (int)((b >> 23) & 0xff);
+    if (ex == 0) return 0;
+    const uint64_t mant = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+    const int s = ex - 150 + sh;
+    if (s >= 0) return s >= 39 ? 0 : (mant << s);
+    const int r = -s;
+    if (r >= 63) return 0;
+    return (mant + (1ull << (r - 1))) >> r;
+}
+
+template <int FMT>
+__device__ __forceinline__ void load_elem(const void* X, int64_t idx, double& d, float& hi, float& lo) {
+    if (FMT == FMT_F64) {
+        d = ((const double*)X)[idx];
+    } else {
+        const float2 p = ((const float2*)X)[idx];
+        hi = p.x;
+        lo = p.y;
+    }
+}
+
+// Slicing: one warp per row.  F = round(X 2^(T - e)) is a signed integer with
+// |F| <= 2^T, T = B1 + 8 (NS - 1); it is cut into NS balanced digits
+// c_0 = round(F / 2^(T - B1)), c_p = round(r_p / 2^(T - B1 - 8p)), the last digit
+// taking the remainder, so that |c_p| <= 128 for every p.  Slice p stores
+// c_p 2^(-8p), exactly representable in BF16.
+template <int FMT>
+__global__ void __launch_bounds__(256) slice_rows_kernel(const void* __restrict__ X, int64_t rows, int K, int64_t ld,
+                                                         int NS, int Kp, __nv_bfloat16* __restrict__ out,
+                                                         int64_t slice_stride, int32_t* __restrict__ exps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const int64_t base = row * ld;
+    int emax = -2000;
+    for (int k = lane; k < K; k += 32) {
+        double d = 0.0;
+        float hi = 0.f, lo = 0.f;
+        load_elem<FMT>(X, base + k, d, hi, lo);
+        const int ex = FMT == FMT_F64 ? exp_f64(d) : exp_f32(hi);
+        emax = max(emax, ex);
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    // |X| < 2^(emax + 1); the FP32-pair rounding margin is absorbed because the
+    // top digit may reach 2^B1 = 128 exactly.
+    const int e = emax <= -2000 ? 0 : emax + 1;
+    if (lane == 0) exps[row] = e;
+    const int T = SLICE_B1 + 8 * (NS - 1);
+    __nv_bfloat16* o0 = out + row * Kp;
+    for (int k = lane; k < Kp; k += 32) {
+        int64_t F = 0;
+        if (k < K && emax > -2000) {
+            double d = 0.0;
+            float hi = 0.f, lo = 0.f;
+            load_elem<FMT>(X, base + k, d, hi, lo);
+            if (FMT == FMT_F64) {
+                const int64_t a = (int64_t)fixed_f64(d, T - e);
+                F = d < 0.0 ? -a : a;
+            } else {
+                const int G = 16;  // guard bits for the exact integer sum hi + lo
+                const int64_t fh = (int64_t)fixed_f32(hi, T - e + G) * (hi < 0.f ? -1 : 1);
+                const int64_t fl = (int64_t)fixed_f32(lo, T - e + G) * (lo < 0.f ? -1 : 1);
+                F = (fh + fl + (1ll << (G - 1))) >> G;
+            }
+        }
+        int64_t r = F;
+        for (int p = 0; p < NS; ++p) {
+            const int sh = 8 * (NS - 1 - p);  // = T - B1 - 8p
+            int64_t c;
+            if (sh == 0) {
+                c = r;
+            } else {
+                c = (r + (1ll << (sh - 1))) >> sh;  // round half up (arithmetic shift)
+                r -= c << sh;
+            }
+            o0[p * slice_stride + k] = __float2bfloat16_rn(ldexpf((float)c, -8 * p));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers (tcgen05, TMA, mbarrier)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr uint32_t WAIT_LIMIT = 1u << 21;  // try_wait rounds before a wait is declared failed
+
+// Bounded wait.  Gives up after WAIT_LIMIT rounds, or as soon as another CTA
+// has recorded a failure in the engine's status word (checked every 256 rounds).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const int32_t* status) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u && *(volatile const int32_t*)status != 0) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with 64-byte swizzle: rows of 64 B, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;               // descriptor version for tcgen05
+    d |= (uint64_t)4 << 61;               // SWIZZLE_64B
+    return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// The GEMM kernel
+// ---------------------------------------------------------------------------
+constexpr int BM = 128;
+constexpr int BN = 128;
+constexpr int BK = 32;  // BF16 elements per stage row (64 bytes)
+constexpr int UK = 16;  // K per tcgen05.mma (kind::f16)
+constexpr int KCB = KCHUNK / BK;  // k-blocks per exactly-accumulated chunk
+constexpr int EPI_WARPS = 8;      // two warps per TMEM lane quadrant, 64 columns each
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+
+template <int NS>
+struct UmmaCfg {
+    static constexpr int A_SLICE = BM * BK * 2;  // bytes of one 128 x 32 BF16 tile
+    static constexpr int B_SLICE = BN * BK * 2;
+    static constexpr int STAGE = NS * (A_SLICE + B_SLICE);
+    static constexpr int STAGES = (200 * 1024) / STAGE >= 4 ? 4 : (200 * 1024) / STAGE;
+    static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int TMEM_COLS = 512;  // acc0 | acc1 | acc2 (3 x 128 used)
+};
+
+struct UmmaArgs {
+    int M, N, Kp;
+    const int32_t* eA;
+    const int32_t* eB;
+    void* C;
+    int64_t ldc;
+    int out_fmt;
+    int group_m;
+    int32_t* status;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+// hi + lo += a0 + a1 + a2, with a0, a1 exact (integer-valued) and a2 small:
+// two error-free TwoSum steps, the rounding errors folded into lo.
+__device__ __forceinline__ void df_accumulate(float& hi, float& lo, float a0, float a1, float a2) {
+    const float s = __fadd_rn(hi, a0);
+    const float bp = __fsub_rn(s, hi);
+    const float e1 = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(a0, bp));
+    const float t = __fadd_rn(s, a1);
+    const float bq = __fsub_rn(t, s);
+    const float e2 = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bq)), __fsub_rn(a1, bq));
+    const float l = __fadd_rn(lo, __fadd_rn(__fadd_rn(e1, e2), a2));
+    const float h = __fadd_rn(t, l);  // renormalise (fast two-sum, |t| >= |l|)
+    lo = __fsub_rn(l, __fsub_rn(h, t));
+    hi = h;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(THREADS, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB, UmmaArgs args) {
+    using Cfg = UmmaCfg<NS>;
+    constexpr int STAGES = Cfg::STAGES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* chunk_full = empty + STAGES;
+    uint64_t* chunk_empty = chunk_full + 1;
+    uint32_t* tmem_slot = (uint32_t*)(chunk_empty + 1);
+    int* s_fail = (int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (args.N + BN - 1) / BN;
+    const int m_tiles = (args.M + BM - 1) / BM;
+    const int pid = blockIdx.x;
+    const int gm = args.group_m;
+    const int group = pid / (gm * n_tiles);
+    const int first_m = group * gm;
+    const int gsize = min(m_tiles - first_m, gm);
+    const int tile_m = first_m + (pid % (gm * n_tiles)) % gsize;
+    const int tile_n = (pid % (gm * n_tiles)) / gsize;
+    const int num_kb = args.Kp / BK;
+    const int n_chunks = (num_kb + KCB - 1) / KCB;
+
+    // another CTA already failed: leave (uniformly) before touching TMEM or issuing copies
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = *(volatile const int32_t*)args.status;
+    __syncthreads();
+    if (s_abort != 0) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(chunk_full, 1);
+        mbar_init(chunk_empty, EPI_WARPS);
+        *s_fail = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < num_kb; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES) {
+                    if (!mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, args.status)) {
+                        *s_fail = 1;
+                        break;
+                    }
+                }
+                uint8_t* sa = smem + s * Cfg::STAGE;
+                uint8_t* sb = sa + NS * Cfg::A_SLICE;
+                mbar_arrive_expect_tx(&full[s], Cfg::STAGE);
+                tma_load_3d(sa, &tmA, &full[s], kb * BK, tile_m * BM, 0);
+                tma_load_3d(sb, &tmB, &full[s], kb * BK, tile_n * BN, 0);
+                ++issued;
+            }
+            // every issued load must have landed before the CTA may exit
+            const int first = issued > STAGES ? issued - STAGES : 0;
+            for (int kb = first; kb < issued; ++kb)
+                if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, args.status)) *s_fail = 1;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            const uint32_t acc0 = tmem, acc1 = tmem + BN, acc2 = tmem + 2 * BN;
+            bool ok = true;
+            for (int kb = 0; kb < num_kb && ok; ++kb) {
+                const int s = kb % STAGES;
+                const int chunk = kb / KCB;
+                const bool chunk_start = (kb % KCB) == 0;
+                if (chunk_start && chunk > 0) {
+                    // the epilogue must have drained the previous chunk's accumulators
+                    if (!mbar_wait(chunk_empty, (chunk - 1) & 1, args.status)) {
+                        *s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                if (!mbar_wait(&full[s], (kb / STAGES) & 1, args.status)) {
+                    *s_fail = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * Cfg::STAGE);
+                const uint32_t sb = sa + NS * Cfg::A_SLICE;
+#pragma unroll
+                for (int kk = 0; kk < BK / UK; ++kk) {
+                    const uint32_t koff = kk * UK * 2;  // bytes along K inside the 64-byte row
+                    const uint32_t keep = (chunk_start && kk == 0) ? 0u : 1u;
+                    // diagonal 0: exact
+                    umma_bf16(acc0, sdesc_sw64(sa + koff), sdesc_sw64(sb + koff), idesc, keep);
+                    // diagonal 1: exact
+                    umma_bf16(acc1, sdesc_sw64(sa + koff), sdesc_sw64(sb + Cfg::B_SLICE + koff), idesc, keep);
+                    umma_bf16(acc1, sdesc_sw64(sa + Cfg::A_SLICE + koff), sdesc_sw64(sb + koff), idesc, 1u);
+                    // diagonals >= 2: 2^-16 below the leading term
+                    bool first2 = keep == 0u;
+#pragma unroll
+                    for (int p = 0; p < NS; ++p) {
+#pragma unroll
+                        for (int q = 0; q < NS; ++q) {
+                            if (p + q < 2 || p + q > NS - 1) continue;
+                            umma_bf16(acc2, sdesc_sw64(sa + p * Cfg::A_SLICE + koff),
+                                      sdesc_sw64(sb + q * Cfg::B_SLICE + koff), idesc, first2 ? 0u : 1u);
+                            first2 = false;
+                        }
+                    }
+                }
+                umma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                if ((kb % KCB) == KCB - 1 || kb == num_kb - 1) umma_commit(chunk_full);
+            }
+            if (!ok) umma_commit(chunk_full);  // release the epilogue; s_fail marks the result invalid
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 and 64 columns
+        const int quad = warp & 3;
+        const int colbase = ((warp - 2) >> 2) * 64;
+        const int row_local = quad * 32 + lane;
+        const int64_t row = (int64_t)tile_m * BM + row_local;
+        float hi[64], lo[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            hi[j] = 0.f;
+            lo[j] = 0.f;
+        }
+        bool alive = true;
+        for (int c = 0; c < n_chunks; ++c) {
+            alive = __all_sync(0xffffffffu, (alive && mbar_wait(chunk_full, c & 1, args.status)) ? 1 : 0) != 0;
+            if (!alive) {
+                *s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                uint32_t r0[8], r1[8], r2[8];
+                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + colbase + g * 8;
+                tmem_ld8(taddr, r0);
+                tmem_ld8(taddr + BN, r1);
+                tmem_ld8(taddr + 2 * BN, r2);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    df_accumulate(hi[g * 8 + j], lo[g * 8 + j], __uint_as_float(r0[j]), __uint_as_float(r1[j]),
+                                  __uint_as_float(r2[j]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(chunk_empty);
+        }
+        if (alive && row < args.M) {
+            const int ea = args.eA[row];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int64_t col = (int64_t)tile_n * BN + colbase + j;
+                if (col < args.N) {
+                    const int sc = ea + args.eB[col] - 2 * SLICE_B1;
+                    if (args.out_fmt == FMT_F64)
+                        ((double*)args.C)[row * args.ldc + col] = ldexp((double)hi[j] + (double)lo[j], sc);
+                    else
+                        ((float2*)args.C)[row * args.ldc + col] = make_float2(ldexpf(hi[j], sc), ldexpf(lo[j], sc));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *s_fail) atomicExch(args.status, (int)HOTRG_ETIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled)p;
+    }
+    return fn;
+}
+
+// 3D map over slices [NS][rows][Kp] BF16, box {BK, box_rows, NS}
+static bool make_map(CUtensorMap* m, const void* base, int NS, int64_t rows, int Kp, int box_rows) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)NS};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)NS};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Slice counts of the split forms.  HOTRG_SPLIT_BF16_FAST: 3 slices
+// everywhere (23 bits, the FP32 accuracy class).  HOTRG_SPLIT_BF16: by default
+// 4 slices (31 bits) for the environments and 5 (39 bits) for the coarse
+// contraction; HOTRG_SPLIT_SLICES="env,coarse" (each 3..5) overrides them.
+static int ns_for(int prec, bool coarse) {
+    static int env_ns = 0, coarse_ns = 0;
+    if (env_ns == 0) {
+        env_ns = 4;
+        coarse_ns = 5;
+        const char* v = getenv("HOTRG_SPLIT_SLICES");
+        int a = 0, b = 0;
+        if (v && sscanf(v, "%d,%d", &a, &b) == 2 && a >= 3 && a <= 5 && b >= 3 && b <= 5) {
+            env_ns = a;
+            coarse_ns = b;
+        }
+    }
+    if (prec == HOTRG_SPLIT_BF16) return coarse ? coarse_ns : env_ns;
+    return 3;
+}
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
 size_t umma_workspace(int prec, int64_t M, int64_t N, int64_t K) {
-    (void)prec; (void)M; (void)N; (void)K;
-    return 0;
+    const int NS = 5;
+    (void)prec;
+    const int64_t Kp = round_up(K, BK);
+    const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
+    return (size_t)(NS * (Mp + Np) * Kp * 2 + (Mp + Np) * 4 + 4096);
+}
+
+template <int NS>
+static hotrg_status launch_umma(hotrg_ctx* ctx, const __nv_bfloat16* As, const __nv_bfloat16* Bs, int M, int N,
+                                int Kp, const UmmaArgs& a) {
+    using Cfg = UmmaCfg<NS>;
+    static bool attr = false;
+    if (!attr) {
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_gemm_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg::SMEM));
+        attr = true;
+    }
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, As, NS, M, Kp, BM) || !make_map(&mB, Bs, NS, N, Kp, BN))
+        return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    umma_gemm_kernel<NS><<<tiles, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
+    HOTRG_LAUNCH_CHECK(ctx, "umma_gemm_kernel");
+    return HOTRG_OK;
+}
+
+static int32_t* g_status = nullptr;  // per-process device status word of the engine
+
+int32_t* umma_status_word(hotrg_ctx* ctx) {
+    if (!g_status) {
+        if (cudaMalloc(&g_status, 64) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemsetAsync(g_status, 0, 64, ctx->stream);
+    }
+    return g_status;
+}
+
+hotrg_status umma_gemm_fmt(hotrg_ctx* ctx, int prec, int M, int N, int K, const void* A, int afmt, int64_t lda,
+                           const void* B, int bfmt, int64_t ldb, void* C, int cfmt, int64_t ldc, bool coarse) {
+    if (!ctx->tc_ok) return set_err(ctx, HOTRG_ENOTSUP, "tensor-core engine needs sm_103");
+    const int NS = ns_for(prec, coarse);
+    const int Kp = (int)round_up(K, BK);
+    const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
+    __nv_bfloat16* As = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * Mp * Kp * 2);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * Np * Kp * 2);
+    int32_t* eA = (int32_t*)ws_alloc(ctx, (size_t)Mp * 4);
+    int32_t* eB = (int32_t*)ws_alloc(ctx, (size_t)Np * 4);
+    if (!As || !Bs || !eA || !eB) return set_err(ctx, HOTRG_ENOMEM, "umma workspace exhausted");
+    int32_t* st = umma_status_word(ctx);
+    if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
+    cudaStream_t s = ctx->stream;
+    const int rows_per_block = 8;
+    if (afmt == FMT_F64)
+        slice_rows_kernel<FMT_F64><<<(M + rows_per_block - 1) / rows_per_block, 256, 0, s>>>(
+            A, M, K, lda, NS, Kp, As, (int64_t)M * Kp, eA);
+    else
+        slice_rows_kernel<FMT_F32PAIR><<<(M + rows_per_block - 1) / rows_per_block, 256, 0, s>>>(
+            A, M, K, lda, NS, Kp, As, (int64_t)M * Kp, eA);
+    if (bfmt == FMT_F64)
+        slice_rows_kernel<FMT_F64><<<(N + rows_per_block - 1) / rows_per_block, 256, 0, s>>>(
+            B, N, K, ldb, NS, Kp, Bs, (int64_t)N * Kp, eB);
+    else
+        slice_rows_kernel<FMT_F32PAIR><<<(N + rows_per_block - 1) / rows_per_block, 256, 0, s>>>(
+            B, N, K, ldb, NS, Kp, Bs, (int64_t)N * Kp, eB);
+    HOTRG_LAUNCH_CHECK(ctx, "slice_rows_kernel");
+    UmmaArgs a;
+    a.M = M;
+    a.N = N;
+    a.Kp = Kp;
+    a.eA = eA;
+    a.eB = eB;
+    a.C = C;
+    a.ldc = ldc;
+    a.out_fmt = cfmt;
+    a.group_m = 16;
+    a.status = st;
+    if (NS == 5) return launch_umma<5>(ctx, As, Bs, M, N, Kp, a);
+    if (NS == 4) return launch_umma<4>(ctx, As, Bs, M, N, Kp, a);
+    return launch_umma<3>(ctx, As, Bs, M, N, Kp, a);
+}
+
+hotrg_status umma_gemm(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, bool coarse) {
+    return umma_gemm_fmt(ctx, prec, M, N, K, A, FMT_F64, lda, B, FMT_F64, ldb, C, FMT_F64, ldc, coarse);
+}
+
+hotrg_status umma_contract(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda,
+                           const double* B, int64_t ldb, double* C, int64_t ldc) {
+    return umma_gemm_fmt(ctx, prec, M, N, K, A, FMT_F64, lda, B, FMT_F64, ldb, C, FMT_F64, ldc, true);
+}
+
+hotrg_status umma_check_status(hotrg_ctx* ctx) {
+    if (!g_status) return HOTRG_OK;
+    int32_t h = 0;
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, g_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h != 0) {
+        cudaMemsetAsync(g_status, 0, 4, ctx->stream);
+        return set_err(ctx, (hotrg_status)h, "tensor-core engine: a bounded wait ran out");
+    }
+    return HOTRG_OK;
 }
 
 }  // namespace hotrg

@@ -94,6 +94,7 @@ struct EigPlan {
     double tol;
     double tie_rtol;
     int env_policy;
+    bool exact;   // FP64 Jacobi on every block (the FP64 form)
 };
 size_t eig_workspace_bytes(int Dh);
 // E[0] = E_L, E[1] = E_R (E[1] may be null when env_policy == 1).  Writes P
@@ -108,5 +109,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
 hotrg_status gemm_engine(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda,
                          const double* B, int64_t ldb, double* C, int64_t ldc, bool coarse);
 size_t gemm_engine_workspace(int prec, int64_t M, int64_t N, int64_t K);
+hotrg_status umma_contract(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda,
+                           const double* B, int64_t ldb, double* C, int64_t ldc);
+hotrg_status umma_check_status(hotrg_ctx* ctx);
 
 }  // namespace hotrg

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libhotrg.so")
 MAX_STEPS = 64
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-FP64, SPLIT_BF16, TF32X3 = 0, 1, 2
+FP64, SPLIT_BF16, SPLIT_BF16_FAST = 0, 1, 2
 T_PURE, T_IMP_M, T_IMP_M1, T_ISING = 0, 1, 2, 3
 
 
@@ -84,6 +84,9 @@ def _load():
     lib.hotrg_run.restype = ctypes.c_int
     lib.hotrg_observables.argtypes = [vp, ctypes.POINTER(Params), i32, f64, f64, f64, ctypes.POINTER(Obs)]
     lib.hotrg_observables.restype = ctypes.c_int
+    lib.hotrg_contract.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.c_int64, vp, ctypes.c_int64, vp,
+                                   ctypes.c_int64]
+    lib.hotrg_contract.restype = ctypes.c_int
     return lib
 
 
@@ -148,6 +151,11 @@ def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
     out = (Obs * n)()
     _check(ctx, lib.hotrg_observables(ctx, arr, n, hb, hbar, dh, out))
     return list(out)
+
+
+def hotrg_contract(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc):
+    return _check(ctx, lib.hotrg_contract(ctx, prec, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb,
+                                          ctypes.c_void_p(C), ldc))
 
 
 class Context:
