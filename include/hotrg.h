@@ -193,6 +193,33 @@ hotrg_status hotrg_contract(hotrg_ctx* ctx, int32_t prec, int32_t M, int32_t N, 
                             const double* A, int64_t lda, const double* B, int64_t ldb,
                             double* C, int64_t ldc);
 
+/* Per-kernel-class timing recorded with CUDA events on the context's stream
+ * (the stream every library kernel runs on).  Classes of the contraction
+ * engine: 0 environment products, 1 coarse contraction (s1, s2, s3), 2 other.
+ * gemm_ms / gemm_flops cover only the GEMM kernel launches themselves (FP64
+ * SIMT or tensor-core), gemm_flops being the algorithmic 2 M N K of each
+ * launch; slice_ms covers the operand-slicing kernels of the split forms;
+ * eig_ms the truncation (eigensolve, selection, projector); step_ms whole
+ * steps.  launches counts every kernel the library launched. */
+typedef struct {
+    int64_t launches;
+    int64_t gemm_calls[3];
+    double gemm_ms[3];
+    double gemm_flops[3];
+    double slice_ms;
+    double eig_ms;
+    double step_ms;
+    int64_t steps;
+} hotrg_profile;
+
+/* Turn event timing on (enable != 0) or off, and reset the counters.
+ * Errors: HOTRG_EINVAL (ctx NULL), HOTRG_ECUDA. */
+hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int32_t enable);
+
+/* Synchronise the context's stream, fold the pending events into the
+ * totals and copy them to *out (host).  Errors: HOTRG_EINVAL, HOTRG_ECUDA. */
+hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out);
+
 /* Text of the last error on this context ("" when none).  Valid until the
  * next call on the same context. */
 const char* hotrg_last_error(hotrg_ctx* ctx);

@@ -24,9 +24,69 @@
 
 namespace hotrg {
 
+std::atomic<long long> g_launches{0};
+
 hotrg_status set_err(hotrg_ctx* ctx, hotrg_status st, const std::string& msg) {
     if (ctx) ctx->last_error = msg;
     return st;
+}
+
+// ---- profiling ------------------------------------------------------------
+int prof_begin(hotrg_ctx* ctx) {
+    Profiler& P = ctx->prof;
+    if (!P.on) return -1;
+    while (P.pool.size() < 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return -1;
+        }
+        P.pool.push_back(e);
+    }
+    ProfMark m;
+    m.a = P.pool.back();
+    P.pool.pop_back();
+    m.b = P.pool.back();
+    P.pool.pop_back();
+    m.cls = -1;
+    m.flops = 0.0;
+    cudaEventRecord(m.a, ctx->stream);
+    P.pending.push_back(m);
+    return (int)P.pending.size() - 1;
+}
+
+void prof_end(hotrg_ctx* ctx, int handle, int cls, double flops) {
+    if (handle < 0) return;
+    ProfMark& m = ctx->prof.pending[handle];
+    cudaEventRecord(m.b, ctx->stream);
+    m.cls = cls;
+    m.flops = flops;
+}
+
+hotrg_status prof_fold(hotrg_ctx* ctx) {
+    Profiler& P = ctx->prof;
+    for (ProfMark& m : P.pending) {
+        float ms = 0.f;
+        if (m.cls >= 0 && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            if (m.cls <= PROF_GEMM_OTHER) {
+                P.tot.gemm_calls[m.cls] += 1;
+                P.tot.gemm_ms[m.cls] += ms;
+                P.tot.gemm_flops[m.cls] += m.flops;
+            } else if (m.cls == PROF_SLICE) {
+                P.tot.slice_ms += ms;
+            } else if (m.cls == PROF_EIG) {
+                P.tot.eig_ms += ms;
+            } else if (m.cls == PROF_STEP) {
+                P.tot.step_ms += ms;
+                P.tot.steps += 1;
+            }
+        }
+        cudaGetLastError();
+        P.pool.push_back(m.a);
+        P.pool.push_back(m.b);
+    }
+    P.pending.clear();
+    return HOTRG_OK;
 }
 
 static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -246,6 +306,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
         !Tb || !W || !W2 || !Tc || (Ti_in && !Ti2) || !partial || !norm)
         return set_err(ctx, HOTRG_ENOMEM, "step workspace exhausted");
     hotrg_status s;
+    const int h_step = prof_begin(ctx);
     if ((s = environment(ctx, prec, T_in, Dh, Dv, false, X1, X2, Am, Bm, A2, B2, Ep, EL)) != HOTRG_OK) return s;
     if (p->env_policy == 0)
         if ((s = environment(ctx, prec, T_in, Dh, Dv, true, X1, X2, Am, Bm, A2, B2, Ep, ER)) != HOTRG_OK) return s;
@@ -259,9 +320,11 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     plan.tie_rtol = p->tie_rtol > 0 ? p->tie_rtol : 1e-12;
     plan.env_policy = p->env_policy;
     plan.exact = prec == HOTRG_FP64;
+    const int h_eig = prof_begin(ctx);
     if ((s = eig_truncate(ctx, plan, EL, p->env_policy == 0 ? ER : nullptr, q_h, P, q_out, info, eigws)) !=
         HOTRG_OK)
         return s;
+    prof_end(ctx, h_eig, PROF_EIG, 0.0);
     if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, T_out)) != HOTRG_OK)
         return s;
     launch_norm(T_out, tn, partial, norm, ctx->stream);
@@ -277,6 +340,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     launch_scale_inv(T_out, tn, norm, ctx->stream);
     launch_step_scalars(norm, info, lnz_acc, weight, ctx->stream);
     HOTRG_LAUNCH_CHECK(ctx, "step");
+    prof_end(ctx, h_step, PROF_STEP, 0.0);
     return HOTRG_OK;
 }
 
@@ -344,6 +408,7 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
     if (imp) launch_scale_inv(Ia, n0, &rd->norm0, st);
     log_kernel<<<1, 32, 0, st>>>(&rd->ln_c0, &rd->norm0);
     log_kernel<<<1, 32, 0, st>>>(&rd->lnz, &rd->norm0);
+    HOTRG_COUNT(2);
     // labels: both legs start with the same labels
     HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(qb, qa, D0 * 4, cudaMemcpyDeviceToDevice, st));
     int32_t* qh = qa;
@@ -377,12 +442,14 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
     if (imp) launch_trace(Icur, Dy, Dx, &rd->tr_imp, st);
     finish_kernel<<<1, 32, 0, st>>>(&rd->lnz, &rd->tr, ldexp(1.0, -p->n_steps), &rd->ln_tr,
                                     imp ? &rd->tr_imp : nullptr, &rd->imp_ratio);
+    HOTRG_COUNT(1);
     HOTRG_LAUNCH_CHECK(ctx, "finish");
     RunDev h;
     HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, rd, sizeof(RunDev), cudaMemcpyDeviceToHost, st));
     HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(out->step, infos, sizeof(hotrg_step_info) * p->n_steps,
                                         cudaMemcpyDeviceToHost, st));
     HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    prof_fold(ctx);
     if (p->prec != HOTRG_FP64)
         if ((s = umma_check_status(ctx)) != HOTRG_OK) { out->status = s; return s; }
     out->lnz_per_site = h.lnz;
@@ -445,6 +512,9 @@ hotrg_status hotrg_create(hotrg_ctx** out, size_t workspace_bytes, void* cuda_st
 
 void hotrg_destroy(hotrg_ctx* ctx) {
     if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    prof_fold(ctx);
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
     if (ctx->ws.base) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->ws.base);
@@ -455,6 +525,25 @@ void hotrg_destroy(hotrg_ctx* ctx) {
 const char* hotrg_last_error(hotrg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
 
 const char* hotrg_version(void) { return "libhotrg 0.1 (sm_103a)"; }
+
+hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int32_t enable) {
+    if (!ctx) return HOTRG_EINVAL;
+    HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_fold(ctx);
+    ctx->prof.on = enable != 0;
+    memset(&ctx->prof.tot, 0, sizeof(ctx->prof.tot));
+    ctx->prof.launch_base = g_launches.load();
+    return HOTRG_OK;
+}
+
+hotrg_status hotrg_profile_read(hotrg_ctx* ctx, hotrg_profile* out) {
+    if (!ctx || !out) return HOTRG_EINVAL;
+    HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_fold(ctx);
+    *out = ctx->prof.tot;
+    out->launches = g_launches.load() - ctx->prof.launch_base;
+    return HOTRG_OK;
+}
 
 hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const hotrg_params* p, int32_t kind, double* T_dev,
                                int32_t* labels_dev) {

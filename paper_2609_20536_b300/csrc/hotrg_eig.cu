@@ -842,6 +842,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
     int small_thr = exact ? n : (bcap > 48 ? bcap : 48);
     if (!exact && thr_override) small_thr = thr_override;
     sectors_kernel<<<1, SORT_THREADS, MAX_N * 8, st>>>(q_h, plan.Dh, plan.sym, small_thr, bcap, w);
+    HOTRG_COUNT(3);  // sectors, jacobi, select
+    HOTRG_COUNT(exact ? 1 : 5);  // projector (+ subspace, rr_prep, rr_product, rr_finish)
     HOTRG_LAUNCH_CHECK(ctx, "sectors_kernel");
     const int sides = plan.env_policy == 0 ? 2 : 1;
     const int grid = n < 2 * ctx->sm_count ? n : 2 * ctx->sm_count;

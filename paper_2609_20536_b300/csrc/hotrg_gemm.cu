@@ -13,7 +13,9 @@ hotrg_status gemm_engine(hotrg_ctx* ctx, int prec, int M, int N, int K, const do
                          int64_t ldb, double* C, int64_t ldc, bool coarse) {
     if (M <= 0 || N <= 0) return HOTRG_OK;
     if (prec == HOTRG_FP64) {
+        const int h = prof_begin(ctx);
         launch_gemm_tn_f64(M, N, K, A, lda, B, ldb, C, ldc, 1, 0, 0, 0, ctx->stream);
+        prof_end(ctx, h, coarse ? PROF_GEMM_COARSE : PROF_GEMM_ENV, 2.0 * M * N * (double)K);
         HOTRG_LAUNCH_CHECK(ctx, "gemm_tn_f64");
         return HOTRG_OK;
     }

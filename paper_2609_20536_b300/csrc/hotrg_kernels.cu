@@ -102,6 +102,7 @@ void launch_init_tensor(const hotrg_params* p, int kind, double* T, int32_t* lab
                         cudaStream_t st) {
     if (kind == HOTRG_T_ISING) {
         ising_tensor_kernel<<<1, 32, 0, st>>>(p->beta, T, labels);
+        HOTRG_COUNT(1);
         return;
     }
     const int n_max = p->n_max;
@@ -117,6 +118,7 @@ void launch_init_tensor(const hotrg_params* p, int kind, double* T, int32_t* lab
     const int total = na * na * na * na;
     gxy_tensor_kernel<<<(total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024, 256, 0, st>>>(
         a, F, n_max, sym, T, labels);
+    HOTRG_COUNT(2);
 }
 
 // ---------------------------------------------------------------------------
@@ -156,6 +158,7 @@ void launch_permute(const double* in, double* out, int nd, const int64_t* od, co
     int64_t blocks = (a.total + 255) / 256;
     if (blocks > 148 * 32) blocks = 148 * 32;
     permute_kernel<<<(int)blocks, 256, 0, st>>>(in, out, a);
+    HOTRG_COUNT(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,6 +226,7 @@ void launch_gemm_tn_f64(int M, int N, int K, const double* A, int64_t lda, const
     if (M <= 0 || N <= 0 || batch <= 0) return;
     dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, batch);
     gemm_tn_f64_kernel<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, sA, sB, sC);
+    HOTRG_COUNT(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -264,6 +268,7 @@ __global__ void sumsq_final_kernel(const double* partial, int np, double* norm) 
 void launch_norm(const double* x, int64_t n, double* partial, double* norm, cudaStream_t st) {
     sumsq_partial_kernel<<<NORM_BLOCKS, 256, 0, st>>>(x, n, partial);
     sumsq_final_kernel<<<1, 256, 0, st>>>(partial, NORM_BLOCKS, norm);
+    HOTRG_COUNT(2);
 }
 
 __global__ void scale_inv_kernel(double* x, int64_t n, const double* c) {
@@ -277,6 +282,7 @@ void launch_scale_inv(double* x, int64_t n, const double* c, cudaStream_t st) {
     if (blocks > 148 * 16) blocks = 148 * 16;
     if (blocks < 1) blocks = 1;
     scale_inv_kernel<<<(int)blocks, 256, 0, st>>>(x, n, c);
+    HOTRG_COUNT(1);
 }
 
 __global__ void axpby_kernel(double* y, const double* x, double a, double b, int64_t n) {
@@ -289,6 +295,7 @@ void launch_axpby(double* y, const double* x, double a, double b, int64_t n, cud
     if (blocks > 148 * 16) blocks = 148 * 16;
     if (blocks < 1) blocks = 1;
     axpby_kernel<<<(int)blocks, 256, 0, st>>>(y, x, a, b, n);
+    HOTRG_COUNT(1);
 }
 
 __global__ void trace_kernel(const double* T, int Dx, int Dy, double* tr) {
@@ -305,6 +312,7 @@ __global__ void trace_kernel(const double* T, int Dx, int Dy, double* tr) {
 
 void launch_trace(const double* T, int Dx, int Dy, double* tr, cudaStream_t st) {
     trace_kernel<<<1, 256, 0, st>>>(T, Dx, Dy, tr);
+    HOTRG_COUNT(1);
 }
 
 __global__ void step_scalars_kernel(const double* norm, hotrg_step_info* info, double* lnz_acc,
@@ -319,6 +327,7 @@ __global__ void step_scalars_kernel(const double* norm, hotrg_step_info* info, d
 void launch_step_scalars(const double* norm, hotrg_step_info* info, double* lnz_acc, double weight,
                          cudaStream_t st) {
     step_scalars_kernel<<<1, 32, 0, st>>>(norm, info, lnz_acc, weight);
+    HOTRG_COUNT(1);
 }
 
 }  // namespace hotrg

@@ -277,6 +277,8 @@ struct UmmaCfg {
 
 struct UmmaArgs {
     int M, N, Kp;
+    int K;           // algorithmic K (before padding), for the flop count
+    int prof_class;
     const int32_t* eA;
     const int32_t* eB;
     void* C;
@@ -581,7 +583,10 @@ static hotrg_status launch_umma(hotrg_ctx* ctx, const __nv_bfloat16* As, const _
     if (!make_map(&mA, As, NS, M, Kp, BM) || !make_map(&mB, Bs, NS, N, Kp, BN))
         return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
     const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const int h = prof_begin(ctx);
     umma_gemm_kernel<NS><<<tiles, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
+    prof_end(ctx, h, a.prof_class, 2.0 * M * N * (double)a.K);
+    HOTRG_COUNT(1);
     HOTRG_LAUNCH_CHECK(ctx, "umma_gemm_kernel");
     return HOTRG_OK;
 }
@@ -614,6 +619,7 @@ hotrg_status umma_gemm_fmt(hotrg_ctx* ctx, int prec, int M, int N, int K, const 
     if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
     cudaStream_t s = ctx->stream;
     const int rows_per_block = 8;
+    const int h_slice = prof_begin(ctx);
     if (afmt == FMT_F64)
         slice_rows_kernel<FMT_F64><<<(M + rows_per_block - 1) / rows_per_block, 256, 0, s>>>(
             A, M, K, lda, NS, Kp, As, (int64_t)M * Kp, eA);
@@ -626,8 +632,12 @@ hotrg_status umma_gemm_fmt(hotrg_ctx* ctx, int prec, int M, int N, int K, const 
     else
         slice_rows_kernel<FMT_F32PAIR><<<(N + rows_per_block - 1) / rows_per_block, 256, 0, s>>>(
             B, N, K, ldb, NS, Kp, Bs, (int64_t)N * Kp, eB);
+    HOTRG_COUNT(2);
+    prof_end(ctx, h_slice, PROF_SLICE, 0.0);
     HOTRG_LAUNCH_CHECK(ctx, "slice_rows_kernel");
     UmmaArgs a;
+    a.K = K;
+    a.prof_class = coarse ? PROF_GEMM_COARSE : PROF_GEMM_ENV;
     a.M = M;
     a.N = N;
     a.Kp = Kp;

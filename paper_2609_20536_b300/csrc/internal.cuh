@@ -4,12 +4,35 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
 #include "../../include/hotrg.h"
 
 namespace hotrg {
+
+// kernels launched by the library (all contexts)
+extern std::atomic<long long> g_launches;
+#define HOTRG_COUNT(n) (::hotrg::g_launches.fetch_add((n), std::memory_order_relaxed))
+
+// profiling classes
+enum ProfClass : int { PROF_GEMM_ENV = 0, PROF_GEMM_COARSE = 1, PROF_GEMM_OTHER = 2, PROF_SLICE = 3, PROF_EIG = 4,
+                       PROF_STEP = 5 };
+
+struct ProfMark {
+    cudaEvent_t a, b;
+    int cls;
+    double flops;
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<ProfMark> pending;
+    hotrg_profile tot{};
+    long long launch_base = 0;
+};
 
 // Symmetry of the fused-leg labels: U(1) charge, Z2 parity, or none.
 enum SymMode : int { SYM_U1 = 0, SYM_Z2 = 1, SYM_NONE = 2 };
@@ -31,6 +54,7 @@ struct hotrg_ctx {
     int sm_count = 148;
     int smem_optin = 0;
     bool tc_ok = false;  // sm_103a tensor-core path usable on this device
+    hotrg::Profiler prof;
 };
 
 namespace hotrg {
@@ -54,6 +78,11 @@ hotrg_status set_err(hotrg_ctx* ctx, hotrg_status st, const std::string& msg);
                                     std::string("launch ") + (what) + ": " +                \
                                         cudaGetErrorString(_e));                            \
     } while (0)
+
+// ---- profiling: bracket a region with prof_begin / prof_end on ctx->stream --
+int prof_begin(hotrg_ctx* ctx);  // returns a handle (-1 when profiling is off)
+void prof_end(hotrg_ctx* ctx, int handle, int cls, double flops);
+hotrg_status prof_fold(hotrg_ctx* ctx);  // after a stream sync: accumulate finished marks
 
 // ---- workspace (bump allocator, 256-byte aligned) -------------------------
 hotrg_status ws_reserve(hotrg_ctx* ctx, size_t bytes);

@@ -54,6 +54,14 @@ class Result(ctypes.Structure):
     ]
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64), ("gemm_calls", ctypes.c_int64 * 3), ("gemm_ms", ctypes.c_double * 3),
+        ("gemm_flops", ctypes.c_double * 3), ("slice_ms", ctypes.c_double), ("eig_ms", ctypes.c_double),
+        ("step_ms", ctypes.c_double), ("steps", ctypes.c_int64),
+    ]
+
+
 class Obs(ctypes.Structure):
     _fields_ = [
         ("lnz", ctypes.c_double), ("f", ctypes.c_double), ("cv", ctypes.c_double),
@@ -87,6 +95,10 @@ def _load():
     lib.hotrg_contract.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.c_int64, vp, ctypes.c_int64, vp,
                                    ctypes.c_int64]
     lib.hotrg_contract.restype = ctypes.c_int
+    lib.hotrg_profile_enable.argtypes = [vp, i32]
+    lib.hotrg_profile_enable.restype = ctypes.c_int
+    lib.hotrg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
+    lib.hotrg_profile_read.restype = ctypes.c_int
     return lib
 
 
@@ -156,6 +168,16 @@ def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
 def hotrg_contract(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc):
     return _check(ctx, lib.hotrg_contract(ctx, prec, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb,
                                           ctypes.c_void_p(C), ldc))
+
+
+def hotrg_profile_enable(ctx, enable=True):
+    return _check(ctx, lib.hotrg_profile_enable(ctx, 1 if enable else 0))
+
+
+def hotrg_profile_read(ctx):
+    out = Profile()
+    _check(ctx, lib.hotrg_profile_read(ctx, ctypes.byref(out)))
+    return out
 
 
 class Context:
