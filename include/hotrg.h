@@ -193,6 +193,36 @@ hotrg_status hotrg_contract(hotrg_ctx* ctx, int32_t prec, int32_t M, int32_t N, 
                             const double* A, int64_t lda, const double* B, int64_t ldb,
                             double* C, int64_t ldc);
 
+/* Allocation-free variant of hotrg_contract for the split forms (the thesis
+ * has no counterpart; this is a library convenience).  It is meant for
+ * callers that cannot allocate device memory: code running while another
+ * allocator owns the whole device memory budget, or code that must not risk
+ * the implicit device-wide synchronisation of cudaMalloc.  It needs no
+ * hotrg_ctx and calls no cudaMalloc, cudaFree or allocating library routine:
+ * its scratch (BF16 operand slices, row exponents and a status word) is one
+ * static 32 MiB device array that every GPU loading the library holds until
+ * the process exits.
+ *   C = A B^T, A (device, M x K FP64, row stride lda), B (device, N x K FP64,
+ *   row stride ldb), C (device, M x N FP64, row stride ldc), prec
+ *   HOTRG_SPLIT_BF16 or HOTRG_SPLIT_BF16_FAST, work on cuda_stream (a
+ *   cudaStream_t, NULL for the legacy default stream).  The call returns
+ *   after C is written (it synchronises the stream to read the status word).
+ * Size limit: with NS = 5 (HOTRG_SPLIT_BF16) or 3 (_FAST), Kp = K rounded up
+ * to 32, Mp and Np = M and N rounded up to 128, the call needs
+ * NS (Mp + Np) Kp 2 + 4 (Mp + Np) bytes (each term rounded up to 256) plus
+ * 256; above 32 MiB it returns HOTRG_EINVAL without launching anything.
+ * The first call on each device looks up the device address of the static
+ * array (cudaGetSymbolAddress) and sets kernel attributes with that device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the array, so calls that overlap on the GPU (other streams,
+ * other host threads) race; each call clears the status word and rewrites
+ * the slices and exponents it reads.  Errors: HOTRG_EINVAL (null pointers,
+ * sizes < 1, K > 16384, strides < K or < N, other prec, too large),
+ * HOTRG_ENOTSUP (not sm_103), HOTRG_ETIMEOUT, HOTRG_ECUDA. */
+hotrg_status hotrg_contract_noalloc(int32_t prec, int32_t M, int32_t N, int32_t K,
+                                    const double* A, int64_t lda, const double* B, int64_t ldb,
+                                    double* C, int64_t ldc, void* cuda_stream);
+
 /* Per-kernel-class timing recorded with CUDA events on the context's stream
  * (the stream every library kernel runs on).  Classes of the contraction
  * engine: 0 environment products, 1 coarse contraction (s1, s2, s3), 2 other.

@@ -32,6 +32,8 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace hotrg {
@@ -675,4 +677,123 @@ hotrg_status umma_check_status(hotrg_ctx* ctx) {
     return HOTRG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the split contraction (hotrg_contract_noalloc).
+//
+// For callers that cannot allocate device memory: code that runs while the
+// device memory budget belongs to another allocator, or that must not risk
+// the implicit device synchronisation of cudaMalloc.  The slices, row
+// exponents and the bounded-wait status word live in one file-scope device
+// array of NOALLOC_SCRATCH_BYTES; every GPU that loads the library holds it
+// until the process exits.  Host code cannot use the array's name as a device
+// address: the address comes from cudaGetSymbolAddress, once per device, with
+// that device current (done by the first call on each device).  All calls on
+// a device share the array, so calls that overlap on the GPU race; the
+// status word is cleared by every call, and the slices and exponents are
+// fully rewritten by every call.
+// ---------------------------------------------------------------------------
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+template <int NS>
+static hotrg_status noalloc_launch(cudaStream_t st, const __nv_bfloat16* As, const __nv_bfloat16* Bs, int M, int N,
+                                   int Kp, const UmmaArgs& a) {
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, As, NS, M, Kp, BM) || !make_map(&mB, Bs, NS, N, Kp, BN)) return HOTRG_ECUDA;
+    const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    umma_gemm_kernel<NS><<<tiles, THREADS, UmmaCfg<NS>::SMEM, st>>>(mA, mB, a);
+    HOTRG_COUNT(1);
+    return cudaGetLastError() == cudaSuccess ? HOTRG_OK : HOTRG_ECUDA;
+}
+
+static hotrg_status noalloc_setup(int dev) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (g_noalloc_ptr[dev]) return HOTRG_OK;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return HOTRG_ECUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return HOTRG_ENOTSUP;
+    if (cudaFuncSetAttribute(umma_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, UmmaCfg<5>::SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(umma_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, UmmaCfg<4>::SMEM) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(umma_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, UmmaCfg<3>::SMEM) !=
+            cudaSuccess)
+        return HOTRG_ECUDA;
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return HOTRG_ECUDA;
+    g_noalloc_ptr[dev] = ptr;
+    return HOTRG_OK;
+}
+
+}  // namespace hotrg
+
+extern "C" hotrg_status hotrg_contract_noalloc(int32_t prec, int32_t M, int32_t N, int32_t K, const double* A,
+                                               int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc,
+                                               void* cuda_stream) {
+    using namespace hotrg;
+    if (!A || !B || !C) return HOTRG_EINVAL;
+    if (prec != HOTRG_SPLIT_BF16 && prec != HOTRG_SPLIT_BF16_FAST) return HOTRG_EINVAL;
+    if (M < 1 || N < 1 || K < 1 || K > 16384 || lda < K || ldb < K || ldc < N) return HOTRG_EINVAL;
+    const int NS = ns_for(prec, true);
+    const int Kp = (int)round_up(K, BK);
+    const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
+    const size_t a_bytes = round_up((int64_t)NS * Mp * Kp * 2, 256), b_bytes = round_up((int64_t)NS * Np * Kp * 2, 256);
+    const size_t ea_bytes = round_up(Mp * 4, 256), eb_bytes = round_up(Np * 4, 256);
+    if (256 + a_bytes + b_bytes + ea_bytes + eb_bytes > NOALLOC_SCRATCH_BYTES) return HOTRG_EINVAL;  // too large
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return HOTRG_ECUDA;
+    }
+    hotrg_status s = noalloc_setup(dev);
+    if (s != HOTRG_OK) {
+        cudaGetLastError();
+        return s;
+    }
+    char* base = (char*)g_noalloc_ptr[dev];
+    int32_t* status = (int32_t*)base;  // first 256 bytes: the status word
+    __nv_bfloat16* As = (__nv_bfloat16*)(base + 256);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)(base + 256 + a_bytes);
+    int32_t* eA = (int32_t*)(base + 256 + a_bytes + b_bytes);
+    int32_t* eB = (int32_t*)(base + 256 + a_bytes + b_bytes + ea_bytes);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (cudaMemsetAsync(status, 0, 4, st) != cudaSuccess) {
+        cudaGetLastError();
+        return HOTRG_ECUDA;
+    }
+    const int rpb = 8;
+    slice_rows_kernel<FMT_F64><<<(M + rpb - 1) / rpb, 256, 0, st>>>(A, M, K, lda, NS, Kp, As, (int64_t)M * Kp, eA);
+    slice_rows_kernel<FMT_F64><<<(N + rpb - 1) / rpb, 256, 0, st>>>(B, N, K, ldb, NS, Kp, Bs, (int64_t)N * Kp, eB);
+    HOTRG_COUNT(2);
+    if (cudaGetLastError() != cudaSuccess) return HOTRG_ECUDA;
+    UmmaArgs a;
+    a.M = M;
+    a.N = N;
+    a.Kp = Kp;
+    a.K = K;
+    a.prof_class = PROF_GEMM_OTHER;
+    a.eA = eA;
+    a.eB = eB;
+    a.C = C;
+    a.ldc = ldc;
+    a.out_fmt = FMT_F64;
+    a.group_m = 16;
+    a.status = status;
+    s = NS == 5 ? noalloc_launch<5>(st, As, Bs, M, N, Kp, a)
+                : (NS == 4 ? noalloc_launch<4>(st, As, Bs, M, N, Kp, a) : noalloc_launch<3>(st, As, Bs, M, N, Kp, a));
+    if (s != HOTRG_OK) return s;
+    int32_t h = 0;
+    if (cudaMemcpyAsync(&h, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return HOTRG_ECUDA;
+    }
+    return h == 0 ? HOTRG_OK : (hotrg_status)h;
+}
+
+namespace hotrg {
 }  // namespace hotrg

@@ -180,6 +180,16 @@ def hotrg_profile_read(ctx):
     return out
 
 
+def hotrg_contract_noalloc(prec, M, N, K, A, lda, B, ldb, C, ldc, stream=0):
+    """Allocation-free split contraction (static device scratch); returns the status code."""
+    f = lib.hotrg_contract_noalloc
+    f.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return f(prec, M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb, ctypes.c_void_p(C), ldc,
+             ctypes.c_void_p(stream or None))
+
+
 class Context:
     """Owns one hotrg_ctx bound to a CUDA stream (0: legacy default)."""
 
