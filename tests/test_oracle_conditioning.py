@@ -1,0 +1,49 @@
+"""Conditioning of the GPU parity points, checked on the oracle alone.
+
+A parity tolerance is only meaningful where the quantity is fixed to that
+tolerance by the arithmetic: if a relative perturbation eta of the input
+tensor (the size of one rounding of the form under test) moves ln Z / N by
+more than the tolerance, two correct programs may disagree by that much.
+Each point is run with the input multiplied by (1 + eta * N(0,1)) for two
+seeds; the largest move must stay at least five times below the tolerance.
+"""
+import numpy as np
+import pytest
+
+from oracle import gxy
+from oracle import hotrg as OH
+
+from parity_points import BATCH_ORACLE, FP64_SHAPES, ILL_CONDITIONED, SPLIT_SHAPES
+
+
+def spread(point, eta, seeds=(1, 2)):
+    beta, delta, nm, dcut, steps = point
+    T0 = gxy.site_tensor(beta, delta, nm)
+    q0 = gxy.leg_charges(nm, "u1")
+    ref = OH.hotrg_run(T0, q0, steps, dcut, "u1").lnz_per_site
+    worst = 0.0
+    for s in seeds:
+        rng = np.random.default_rng(s)
+        Tp = T0 * (1.0 + eta * rng.standard_normal(T0.shape))
+        worst = max(worst, abs(OH.hotrg_run(Tp, q0, steps, dcut, "u1").lnz_per_site - ref))
+    return worst
+
+
+@pytest.mark.parametrize("point", FP64_SHAPES)
+def test_fp64_points_are_well_conditioned(point):
+    assert spread(point, 1e-15) <= 2e-12
+
+
+@pytest.mark.parametrize("point", SPLIT_SHAPES + BATCH_ORACLE)
+def test_split_points_are_well_conditioned(point):
+    # the split form's per-step ln c_k are accurate to ~1e-10 relative
+    assert spread(point, 1e-10) <= 2e-10
+
+
+def test_ill_conditioned_counter_example():
+    # the same model and cut, four steps further: rounding-level noise is
+    # amplified past any FP64 parity tolerance
+    assert spread(ILL_CONDITIONED, 1e-15) > 1e-9
+    short = ILL_CONDITIONED[:4] + (10,)
+    assert spread(short, 1e-15) <= 2e-12
+    assert spread(short, 1e-10) > 1e-9
