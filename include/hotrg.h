@@ -87,6 +87,9 @@ typedef struct {
     int32_t tkind;       /* hotrg_tkind of the pure tensor: HOTRG_T_PURE or HOTRG_T_ISING */
     double tie_rtol;     /* cut-cluster width relative to lambda_max (default 1e-12 when <= 0) */
     double eig_tol;      /* Jacobi stop: off-diagonal Frobenius <= eig_tol * ||E_q||_F (1e-15 when <= 0) */
+    double side_rtol;    /* eps_2 wins only if eps_2 < eps_1 (1 - side_rtol) (default 1e-6 when <= 0):
+                            mirror-image environments give eps_1 = eps_2, which must not be decided by
+                            the rounding of the eigenvalue sums */
 } hotrg_params;
 
 /* Per-step scalars (device- or host-resident, see each entry point). */
@@ -135,7 +138,8 @@ hotrg_status hotrg_create(hotrg_ctx** ctx, size_t workspace_bytes, void* cuda_st
 /* Release the context and its workspace.  NULL is a no-op. */
 void hotrg_destroy(hotrg_ctx* ctx);
 
-/* Build the initial site tensor (Eq. 3.4 coefficients with the own Bessel
+/* Build the initial site tensor (synchronous: returns once the tensor is
+ * written) (Eq. 3.4 coefficients with the own Bessel
  * series on the device; Eq. 3.15 / 3.20 / 3.21 field and impurity factors)
  * into T_dev (device, D0^4 FP64, [l][r][u][d], D0 = 2 n_max + 1; for
  * HOTRG_T_ISING D0 = 2) and the D0 bond labels into labels_dev (device,
@@ -172,6 +176,19 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, const hotrg_params* p,
  * its own).  Synchronous. */
 hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
                        int32_t imp_kind, hotrg_result* out);
+
+/* Batched points: the same results as hotrg_run, computed concurrently on
+ * nstreams worker streams (1..16, created by the context, each with its own
+ * workspace).  Points are sorted by cost (longest first, the s2 work of
+ * every step) and each goes to the least-loaded worker.  The first point of
+ * a class (every parameter except beta, Delta and the values -- not the
+ * zero pattern -- of h, h1) on a worker runs directly; its sequence of
+ * kernels is then captured once into a CUDA graph that later points of the
+ * class replay, with beta, Delta, h, h1 fed through a device parameter slot.
+ * params, out: host arrays of npoints.  Synchronous.  Returns the first
+ * non-OK status (each out[i].status holds its own). */
+hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
+                             int32_t imp_kind, int32_t nstreams, hotrg_result* out);
 
 /* Observables of npoints points (§3.4): ln Z/N and f at zero field;
  * C_V = beta^2 [l(beta+hb) - 2 l(beta) + l(beta-hb)] / hb^2 (Eq. 3.17);
@@ -223,6 +240,34 @@ hotrg_status hotrg_contract_noalloc(int32_t prec, int32_t M, int32_t N, int32_t 
                                     const double* A, int64_t lda, const double* B, int64_t ldb,
                                     double* C, int64_t ldc, void* cuda_stream);
 
+/* Surrogate network (no counterpart in the thesis): an ensemble of MLPs
+ * 2 -> 128 -> 128 -> 128 -> 4 (tanh hidden layers, linear output) mapping
+ * standardised (beta, Delta) to standardised (f, C_V, chi, chi1).  Weights
+ * are used in BF16 by every product, which accumulates in FP32; Adam keeps
+ * FP32 master weights.  Parameters are laid out flat per member as
+ * [W_0 b_0 W_1 b_1 W_2 b_2 W_3 b_3] with W_l row-major [in][out]
+ * (hotrg_mlp_num_params() floats).  All buffers named X, T, mean, spread,
+ * flat are host arrays (X: n x 2, T / mean / spread: n x 4, row-major). */
+typedef struct hotrg_mlp hotrg_mlp;
+
+/* ensemble in [1, 16]; seed fixes the initialisation (Glorot uniform, zero
+ * biases) and the minibatch order. */
+hotrg_status hotrg_mlp_create(hotrg_mlp** m, int32_t ensemble, uint64_t seed, void* cuda_stream);
+void hotrg_mlp_destroy(hotrg_mlp* m);
+int64_t hotrg_mlp_num_params(void);
+hotrg_status hotrg_mlp_set_params(hotrg_mlp* m, int32_t member, const float* flat);
+hotrg_status hotrg_mlp_get_params(hotrg_mlp* m, int32_t member, float* flat);
+/* Loss (mean squared error) and its gradient for one member on n <= 4096
+ * samples (gradient written to grad_flat when not NULL). */
+hotrg_status hotrg_mlp_gradients(hotrg_mlp* m, int32_t member, const float* X, const float* T, int32_t n,
+                                 float* loss, float* grad_flat);
+/* epochs of Adam (learning rate lr) over minibatches of batch <= 4096 for
+ * every member; final_loss: the members' mean loss on the last minibatch. */
+hotrg_status hotrg_mlp_train(hotrg_mlp* m, const float* X, const float* T, int32_t n, int32_t epochs,
+                             int32_t batch, float lr, float* final_loss);
+/* Ensemble mean and spread (standard deviation over members) per output. */
+hotrg_status hotrg_mlp_predict(hotrg_mlp* m, const float* X, int32_t n, float* mean, float* spread);
+
 /* Per-kernel-class timing recorded with CUDA events on the context's stream
  * (the stream every library kernel runs on).  Classes of the contraction
  * engine: 0 environment products, 1 coarse contraction (s1, s2, s3), 2 other.
@@ -240,6 +285,7 @@ typedef struct {
     double eig_ms;
     double step_ms;
     int64_t steps;
+    double eig_part_ms[4]; /* block discovery + Jacobi; FP32 subspace; FP64 Rayleigh-Ritz; selection + projector */
 } hotrg_profile;
 
 /* Turn event timing on (enable != 0) or off, and reset the counters.

@@ -15,9 +15,11 @@
 // operands are laid out by permutation kernels.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "internal.cuh"
@@ -79,6 +81,8 @@ hotrg_status prof_fold(hotrg_ctx* ctx) {
             } else if (m.cls == PROF_STEP) {
                 P.tot.step_ms += ms;
                 P.tot.steps += 1;
+            } else if (m.cls >= PROF_EIG_PART0 && m.cls < PROF_EIG_PART0 + 4) {
+                P.tot.eig_part_ms[m.cls - PROF_EIG_PART0] += ms;
             }
         }
         cudaGetLastError();
@@ -237,6 +241,38 @@ static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, in
                            double* Tb, double* W, double* W2, double* Tc, double* T_out) {
     const int64_t hh = (int64_t)Dh * Dh, vv = (int64_t)Dv * Dv;
     hotrg_status s;
+    static int no_gather = -1;  // HOTRG_NO_GATHER=1: permuted copies instead of gather maps (diagnosis)
+    if (no_gather < 0) {
+        const char* v = getenv("HOTRG_NO_GATHER");
+        no_gather = (v && v[0] == '1') ? 1 : 0;
+    }
+    if (prec != HOTRG_FP64 && !no_gather) {
+        // split forms: every operand is sliced straight out of its tensor through a gather map
+        // {rd1, rd2, rs0, rs1, rs2, kd, ks0, ks1}; no D^5 permutation is materialised.
+        const int64_t BIG = 1 << 30;
+        const int64_t h = Dh, v = Dv, p = Dp;
+        // s1: W[(x,l2),(r1,u,i)] = sum_l1 P[l1][l2][x] T_up[l1][(r1,u,i)]
+        const int64_t a1[8] = {1, h, 1, 0, p, BIG, 0, h * p};
+        const int64_t b1[8] = {1, 1, 1, 0, 0, BIG, 0, h * vv};
+        if ((s = umma_contract_gather(ctx, prec, (int)(p * h), (int)(h * vv), Dh, P, a1, T_up, b1, W, h * vv,
+                                      true)) != HOTRG_OK)
+            return s;
+        // s2: Z'[(x,r1,u),(d,r2)] = sum_{(l2,i)} W[x][l2][r1][u][i] T_dn[l2][r2][i][d]
+        const int64_t a2[8] = {h, v, hh * vv, vv, v, v, h * vv, 1};
+        const int64_t b2[8] = {1, h, 1, 0, vv, v, h * vv, v};
+        double* Z = W2;
+        if ((s = umma_contract_gather(ctx, prec, (int)(p * h * v), (int)(v * h), (int)(h * v), W, a2, T_dn, b2, Z,
+                                      v * h, true)) != HOTRG_OK)
+            return s;
+        // s3: Tc[(x,u,d),x'] = sum_{(r1,r2)} Z'[x][r1][u][d][r2] P[r1][r2][x']
+        const int64_t a3[8] = {v, v, h * vv * h, v * h, h, h, vv * h, 1};
+        const int64_t b3[8] = {1, 1, 1, 0, 0, BIG, 0, p};
+        if ((s = umma_contract_gather(ctx, prec, (int)(p * vv), Dp, (int)hh, Z, a3, P, b3, Tc, p, true)) != HOTRG_OK)
+            return s;
+        Perm po{4, {Dv, Dv, Dp, Dp}, {(int64_t)Dv * Dp, Dp, vv * Dp, 1}};
+        permute(ctx, Tc, T_out, po);
+        return HOTRG_OK;
+    }
     // s1: W[(x,l2),(r1,u,i)] = Pt[(x,l2),l1] . Tt[(r1,u,i),l1]
     Perm pp{3, {Dp, Dh, Dh}, {1, Dp, (int64_t)Dh * Dp}};
     permute(ctx, P, Pt, pp);
@@ -318,6 +354,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     plan.max_sweeps = p->eig_max_sweeps > 0 ? p->eig_max_sweeps : 40;
     plan.tol = p->eig_tol > 0 ? p->eig_tol : 1e-15;
     plan.tie_rtol = p->tie_rtol > 0 ? p->tie_rtol : 1e-12;
+    plan.side_rtol = p->side_rtol > 0 ? p->side_rtol : 1e-6;
     plan.env_policy = p->env_policy;
     plan.exact = prec == HOTRG_FP64;
     const int h_eig = prof_begin(ctx);
@@ -362,71 +399,107 @@ struct RunDev {
     double lnz, ln_c0, ln_tr, imp_ratio, tr, tr_imp, norm0;
 };
 
-static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kind, hotrg_result* out) {
-    memset(out, 0, sizeof(*out));
-    hotrg_status s = check_params(ctx, p);
-    if (s != HOTRG_OK) { out->status = s; return (hotrg_status)out->status; }
-    const int D0 = d0_of(p);
-    const bool imp = imp_kind == HOTRG_T_IMP_M || imp_kind == HOTRG_T_IMP_M1;
-    if (imp && p->tkind == HOTRG_T_ISING) { out->status = set_err(ctx, HOTRG_EINVAL, "no Ising impurity"); return (hotrg_status)out->status; }
+// Buffers and sizes of one point; carved deterministically from the workspace
+// base, so equal classes get equal addresses (a captured graph stays valid).
+struct PointPlan {
+    int D0 = 0;
+    bool imp = false;
     std::vector<int> dh, dv;
-    step_sizes(p, D0, dh, dv);
-    size_t tmax = (size_t)D0 * D0 * D0 * D0, smax = 0;
-    for (size_t k = 0; k < dh.size(); ++k) {
-        const size_t Dp = std::min<size_t>(p->d_cut, (size_t)dh[k] * dh[k]);
-        tmax = std::max(tmax, Dp * Dp * dv[k] * dv[k]);
-        smax = std::max(smax, step_bytes(p, dh[k], dv[k], imp));
+    int qmax = 0;
+    double *Ta = nullptr, *Tb = nullptr, *Ia = nullptr, *Ib = nullptr;
+    int32_t *qa = nullptr, *qb = nullptr, *qspare = nullptr;
+    double* scratch = nullptr;
+    hotrg_step_info* infos = nullptr;
+    RunDev* rd = nullptr;
+    double* partial = nullptr;
+    hotrg_params* dparams = nullptr;
+    size_t step_base = 0;
+    size_t bytes = 0;
+};
+
+static size_t point_bytes(const hotrg_params* p, int imp_kind, PointPlan& pl) {
+    pl.D0 = d0_of(p);
+    pl.imp = imp_kind == HOTRG_T_IMP_M || imp_kind == HOTRG_T_IMP_M1;
+    pl.dh.clear();
+    pl.dv.clear();
+    step_sizes(p, pl.D0, pl.dh, pl.dv);
+    size_t tmax = (size_t)pl.D0 * pl.D0 * pl.D0 * pl.D0, smax = 0;
+    for (size_t k = 0; k < pl.dh.size(); ++k) {
+        const size_t Dp = std::min<size_t>(p->d_cut, (size_t)pl.dh[k] * pl.dh[k]);
+        tmax = std::max(tmax, Dp * Dp * pl.dv[k] * pl.dv[k]);
+        smax = std::max(smax, step_bytes(p, pl.dh[k], pl.dv[k], pl.imp));
     }
-    const int qmax = std::max(D0, p->d_cut) + 1;
-    const size_t fixed = a256(tmax * 8) * (imp ? 4 : 2) + a256(qmax * 4) * 3 + a256(16384) +
-                         a256(sizeof(hotrg_step_info) * HOTRG_MAX_STEPS) + a256(sizeof(RunDev)) + a256(8192);
-    if ((s = ws_reserve(ctx, fixed + smax)) != HOTRG_OK) { out->status = s; return (hotrg_status)out->status; }
-    double* Ta = (double*)ws_alloc(ctx, tmax * 8);
-    double* Tb = (double*)ws_alloc(ctx, tmax * 8);
-    double* Ia = imp ? (double*)ws_alloc(ctx, tmax * 8) : nullptr;
-    double* Ib = imp ? (double*)ws_alloc(ctx, tmax * 8) : nullptr;
-    int32_t* qa = (int32_t*)ws_alloc(ctx, qmax * 4);
-    int32_t* qb = (int32_t*)ws_alloc(ctx, qmax * 4);
-    double* scratch = (double*)ws_alloc(ctx, 16384);  // coefficient scratch: 2 x 1024 doubles
-    hotrg_step_info* infos = (hotrg_step_info*)ws_alloc(ctx, sizeof(hotrg_step_info) * HOTRG_MAX_STEPS);
-    RunDev* rd = (RunDev*)ws_alloc(ctx, sizeof(RunDev));
-    double* partial = (double*)ws_alloc(ctx, 4096 * 2);
-    const size_t step_base = ctx->ws.used;
+    pl.qmax = std::max(pl.D0, p->d_cut) + 1;
+    const size_t fixed = a256(tmax * 8) * (pl.imp ? 4 : 2) + a256(pl.qmax * 4) * 3 + a256(16384) +
+                         a256(sizeof(hotrg_step_info) * HOTRG_MAX_STEPS) + a256(sizeof(RunDev)) + a256(8192) +
+                         a256(sizeof(hotrg_params));
+    pl.bytes = fixed + smax;
+    return tmax;
+}
+
+// Validate, reserve (may synchronise and grow the workspace; never while
+// capturing) and carve the point's buffers.
+static hotrg_status plan_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kind, PointPlan& pl,
+                               size_t reserve_at_least) {
+    hotrg_status s = check_params(ctx, p);
+    if (s != HOTRG_OK) return s;
+    const bool imp = imp_kind == HOTRG_T_IMP_M || imp_kind == HOTRG_T_IMP_M1;
+    if (imp && p->tkind == HOTRG_T_ISING) return set_err(ctx, HOTRG_EINVAL, "no Ising impurity");
+    const size_t tmax = point_bytes(p, imp_kind, pl);
+    if ((s = ws_reserve(ctx, std::max(pl.bytes, reserve_at_least))) != HOTRG_OK) return s;
+    pl.Ta = (double*)ws_alloc(ctx, tmax * 8);
+    pl.Tb = (double*)ws_alloc(ctx, tmax * 8);
+    pl.Ia = pl.imp ? (double*)ws_alloc(ctx, tmax * 8) : nullptr;
+    pl.Ib = pl.imp ? (double*)ws_alloc(ctx, tmax * 8) : nullptr;
+    pl.qa = (int32_t*)ws_alloc(ctx, pl.qmax * 4);
+    pl.qb = (int32_t*)ws_alloc(ctx, pl.qmax * 4);
+    pl.qspare = (int32_t*)ws_alloc(ctx, pl.qmax * 4);
+    pl.scratch = (double*)ws_alloc(ctx, 16384);  // coefficient scratch: 2 x 1024 doubles
+    pl.infos = (hotrg_step_info*)ws_alloc(ctx, sizeof(hotrg_step_info) * HOTRG_MAX_STEPS);
+    pl.rd = (RunDev*)ws_alloc(ctx, sizeof(RunDev));
+    pl.partial = (double*)ws_alloc(ctx, 4096 * 2);
+    pl.dparams = (hotrg_params*)ws_alloc(ctx, sizeof(hotrg_params));
+    if (!pl.Ta || !pl.Tb || (pl.imp && (!pl.Ia || !pl.Ib)) || !pl.qa || !pl.qb || !pl.qspare || !pl.dparams)
+        return set_err(ctx, HOTRG_ENOMEM, "point workspace");
+    pl.step_base = ctx->ws.used;
+    return HOTRG_OK;
+}
+
+// Every device operation of one point, reading beta / Delta / h / h1 from
+// pl.dparams: no host synchronisation and no allocation, so it can be captured.
+static hotrg_status enqueue_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kind, PointPlan& pl) {
     cudaStream_t st = ctx->stream;
-    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(rd, 0, sizeof(RunDev), st));
-    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(infos, 0, sizeof(hotrg_step_info) * HOTRG_MAX_STEPS, st));
-    launch_init_tensor(p, p->tkind, Ta, qa, scratch, st);
-    if (imp) {
-        int32_t* qdummy = qb;
-        launch_init_tensor(p, imp_kind, Ia, qdummy, scratch + 1024, st);
-    }
+    const int D0 = pl.D0;
+    const bool imp = pl.imp;
+    hotrg_status s;
+    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(pl.rd, 0, sizeof(RunDev), st));
+    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(pl.infos, 0, sizeof(hotrg_step_info) * HOTRG_MAX_STEPS, st));
+    launch_init_tensor(p, pl.dparams, p->tkind, pl.Ta, pl.qa, pl.scratch, st);
+    if (imp) launch_init_tensor(p, pl.dparams, imp_kind, pl.Ia, pl.qb, pl.scratch + 1024, st);
     HOTRG_LAUNCH_CHECK(ctx, "init tensor");
     // c_0 = ||T0||_F; T <- T / c_0 (impurity scaled by the same c_0)
     const int64_t n0 = (int64_t)D0 * D0 * D0 * D0;
-    launch_norm(Ta, n0, partial, &rd->norm0, st);
-    launch_scale_inv(Ta, n0, &rd->norm0, st);
-    if (imp) launch_scale_inv(Ia, n0, &rd->norm0, st);
-    log_kernel<<<1, 32, 0, st>>>(&rd->ln_c0, &rd->norm0);
-    log_kernel<<<1, 32, 0, st>>>(&rd->lnz, &rd->norm0);
+    launch_norm(pl.Ta, n0, pl.partial, &pl.rd->norm0, st);
+    launch_scale_inv(pl.Ta, n0, &pl.rd->norm0, st);
+    if (imp) launch_scale_inv(pl.Ia, n0, &pl.rd->norm0, st);
+    log_kernel<<<1, 32, 0, st>>>(&pl.rd->ln_c0, &pl.rd->norm0);
+    log_kernel<<<1, 32, 0, st>>>(&pl.rd->lnz, &pl.rd->norm0);
     HOTRG_COUNT(2);
     // labels: both legs start with the same labels
-    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(qb, qa, D0 * 4, cudaMemcpyDeviceToDevice, st));
-    int32_t* qh = qa;
-    int32_t* qv = qb;
-    int32_t* qspare = (int32_t*)ws_alloc(ctx, qmax * 4);
-    if (!qspare) { out->status = set_err(ctx, HOTRG_ENOMEM, "label buffer"); return (hotrg_status)out->status; }
-    const size_t step_base2 = ctx->ws.used;
-    (void)step_base;
-    double* Tcur = Ta;
-    double* Tnext = Tb;
-    double* Icur = Ia;
-    double* Inext = Ib;
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(pl.qb, pl.qa, D0 * 4, cudaMemcpyDeviceToDevice, st));
+    int32_t* qh = pl.qa;
+    int32_t* qv = pl.qb;
+    int32_t* qspare = pl.qspare;
+    double* Tcur = pl.Ta;
+    double* Tnext = pl.Tb;
+    double* Icur = pl.Ia;
+    double* Inext = pl.Ib;
     for (int k = 0; k < p->n_steps; ++k) {
-        ctx->ws.used = step_base2;
+        ctx->ws.used = pl.step_base;
         int dp = 0;
-        s = do_step(ctx, p, Tcur, qh, qv, dh[k], dv[k], Tnext, qspare, &dp, &infos[k], Icur, Inext, &rd->lnz,
-                    ldexp(1.0, -(k + 1)));
-        if (s != HOTRG_OK) { out->status = s; return (hotrg_status)out->status; }
+        s = do_step(ctx, p, Tcur, qh, qv, pl.dh[k], pl.dv[k], Tnext, qspare, &dp, &pl.infos[k], Icur, Inext,
+                    &pl.rd->lnz, ldexp(1.0, -(k + 1)));
+        if (s != HOTRG_OK) return s;
         // new horizontal labels = old vertical labels; new vertical = q_out
         int32_t* old_h = qh;
         qh = qv;
@@ -435,27 +508,25 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
         std::swap(Tcur, Tnext);
         std::swap(Icur, Inext);
     }
-    const int Dx = p->n_steps == 0 ? D0 : (int)std::min<long>(p->d_cut, (long)dh.back() * dh.back());
-    const int Dy = p->n_steps == 0 ? D0 : dv.back();
+    const int Dx = p->n_steps == 0 ? D0 : (int)std::min<long>(p->d_cut, (long)pl.dh.back() * pl.dh.back());
+    const int Dy = p->n_steps == 0 ? D0 : pl.dv.back();
     // the final tensor is [Dy][Dy][Dx][Dx] after relabelling (l,r legs = old vertical)
-    launch_trace(Tcur, Dy, Dx, &rd->tr, st);
-    if (imp) launch_trace(Icur, Dy, Dx, &rd->tr_imp, st);
-    finish_kernel<<<1, 32, 0, st>>>(&rd->lnz, &rd->tr, ldexp(1.0, -p->n_steps), &rd->ln_tr,
-                                    imp ? &rd->tr_imp : nullptr, &rd->imp_ratio);
+    launch_trace(Tcur, Dy, Dx, &pl.rd->tr, st);
+    if (imp) launch_trace(Icur, Dy, Dx, &pl.rd->tr_imp, st);
+    finish_kernel<<<1, 32, 0, st>>>(&pl.rd->lnz, &pl.rd->tr, ldexp(1.0, -p->n_steps), &pl.rd->ln_tr,
+                                    imp ? &pl.rd->tr_imp : nullptr, &pl.rd->imp_ratio);
     HOTRG_COUNT(1);
     HOTRG_LAUNCH_CHECK(ctx, "finish");
-    RunDev h;
-    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, rd, sizeof(RunDev), cudaMemcpyDeviceToHost, st));
-    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(out->step, infos, sizeof(hotrg_step_info) * p->n_steps,
-                                        cudaMemcpyDeviceToHost, st));
-    HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    prof_fold(ctx);
-    if (p->prec != HOTRG_FP64)
-        if ((s = umma_check_status(ctx)) != HOTRG_OK) { out->status = s; return s; }
+    return HOTRG_OK;
+}
+
+// Unpack a finished point (host copies of its RunDev and step records).
+static hotrg_status unpack_point(hotrg_ctx* ctx, const hotrg_params* p, const PointPlan& pl, const RunDev& h,
+                                 hotrg_result* out) {
     out->lnz_per_site = h.lnz;
     out->ln_c0 = h.ln_c0;
     out->ln_trace = h.ln_tr;
-    out->imp_ratio = imp ? h.imp_ratio : 0.0;
+    out->imp_ratio = pl.imp ? h.imp_ratio : 0.0;
     out->n_steps = p->n_steps;
     out->status = HOTRG_OK;
     for (int k = 0; k < p->n_steps; ++k)
@@ -471,9 +542,109 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
     return HOTRG_OK;
 }
 
+static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kind, hotrg_result* out) {
+    memset(out, 0, sizeof(*out));
+    PointPlan pl;
+    hotrg_status s = plan_point(ctx, p, imp_kind, pl, 0);
+    if (s != HOTRG_OK) {
+        out->status = s;
+        return s;
+    }
+    cudaStream_t st = ctx->stream;
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(pl.dparams, p, sizeof(hotrg_params), cudaMemcpyHostToDevice, st));
+    if ((s = enqueue_point(ctx, p, imp_kind, pl)) != HOTRG_OK) {
+        out->status = s;
+        return s;
+    }
+    RunDev h;
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, pl.rd, sizeof(RunDev), cudaMemcpyDeviceToHost, st));
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(out->step, pl.infos, sizeof(hotrg_step_info) * p->n_steps,
+                                        cudaMemcpyDeviceToHost, st));
+    HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    prof_fold(ctx);
+    if (p->prec != HOTRG_FP64)
+        if ((s = umma_check_status(ctx)) != HOTRG_OK) {
+            out->status = s;
+            return s;
+        }
+    return unpack_point(ctx, p, pl, h, out);
+}
+
+// ---------------------------------------------------------------------------
+// Batched points: LPT over worker streams, one CUDA graph per point class.
+// ---------------------------------------------------------------------------
+struct ClassKey {
+    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z;
+    double tie_rtol, eig_tol;
+    bool operator==(const ClassKey& o) const { return memcmp(this, &o, sizeof(ClassKey)) == 0; }
+};
+
+static ClassKey class_of(const hotrg_params* p, int imp_kind) {
+    ClassKey k;
+    memset(&k, 0, sizeof(k));
+    k.n_max = p->n_max;
+    k.d_cut = p->d_cut;
+    k.n_steps = p->n_steps;
+    k.prec = p->prec;
+    k.env_policy = p->env_policy;
+    k.tkind = p->tkind;
+    k.m_range = p->m_range;
+    k.eig_max_sweeps = p->eig_max_sweeps;
+    k.imp_kind = imp_kind;
+    k.hz = p->h == 0.0;
+    k.h1z = p->h1 == 0.0;
+    k.tie_rtol = p->tie_rtol;
+    k.eig_tol = p->eig_tol;
+    return k;
+}
+
+static double point_cost(const hotrg_params* p) {
+    std::vector<int> dh, dv;
+    step_sizes(p, d0_of(p), dh, dv);
+    double c = 0.0;
+    for (size_t k = 0; k < dh.size(); ++k) {
+        const double Dp = std::min<double>(p->d_cut, (double)dh[k] * dh[k]);
+        c += Dp * std::pow((double)dh[k], 3) * std::pow((double)dv[k], 3) + 1e6;  // s2 flops + fixed cost
+    }
+    return c;
+}
+
+struct Worker {
+    hotrg_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    struct Graph {
+        ClassKey key;
+        cudaGraphExec_t exec;
+        PointPlan plan;
+        long long launches;
+    };
+    std::vector<Graph> graphs;
+};
+
+struct Batch {
+    std::vector<Worker> workers;
+    size_t reserve = 0;
+};
+
+static void batch_free(Batch* b) {
+    if (!b) return;
+    for (Worker& w : b->workers) {
+        for (auto& g : w.graphs) cudaGraphExecDestroy(g.exec);
+        if (w.ctx) {
+            cudaStreamSynchronize(w.stream);
+            if (w.ctx->ws.base) cudaFree(w.ctx->ws.base);
+            for (cudaEvent_t e : w.ctx->prof.pool) cudaEventDestroy(e);
+            delete w.ctx;
+        }
+        if (w.stream) cudaStreamDestroy(w.stream);
+    }
+    delete b;
+}
+
 }  // namespace hotrg
 
 using namespace hotrg;
+
 
 extern "C" {
 
@@ -512,6 +683,7 @@ hotrg_status hotrg_create(hotrg_ctx** out, size_t workspace_bytes, void* cuda_st
 
 void hotrg_destroy(hotrg_ctx* ctx) {
     if (!ctx) return;
+    batch_free((Batch*)ctx->batch);
     cudaStreamSynchronize(ctx->stream);
     prof_fold(ctx);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
@@ -559,8 +731,12 @@ hotrg_status hotrg_init_tensor(hotrg_ctx* ctx, const hotrg_params* p, int32_t ki
     if (kind < HOTRG_T_PURE || kind > HOTRG_T_ISING) return set_err(ctx, HOTRG_EINVAL, "unknown tensor kind");
     if ((s = ws_reserve(ctx, 16384)) != HOTRG_OK) return s;
     double* scratch = (double*)ws_alloc(ctx, 8192);
-    launch_init_tensor(&q, kind, T_dev, labels_dev, scratch, ctx->stream);
+    hotrg_params* dq = (hotrg_params*)ws_alloc(ctx, sizeof(hotrg_params));
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(dq, &q, sizeof(hotrg_params), cudaMemcpyHostToDevice, ctx->stream));
+    launch_init_tensor(&q, dq, kind, T_dev, labels_dev, scratch, ctx->stream);
     HOTRG_LAUNCH_CHECK(ctx, "init tensor");
+    // the parameter slot is read by the kernels before the call returns to the workspace's next user
+    HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return HOTRG_OK;
 }
 
@@ -614,6 +790,179 @@ hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoin
         if (s != HOTRG_OK && first == HOTRG_OK) first = s;
     }
     return first;
+}
+
+hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints, int32_t imp_kind,
+                             int32_t nstreams, hotrg_result* out) {
+    if (!ctx) return HOTRG_EINVAL;
+    ctx->last_error.clear();
+    if (!params || !out || npoints < 0) return set_err(ctx, HOTRG_EINVAL, "bad arguments");
+    if (nstreams < 1 || nstreams > 16) return set_err(ctx, HOTRG_EINVAL, "nstreams must lie in [1, 16]");
+    if (imp_kind != HOTRG_T_PURE && imp_kind != HOTRG_T_IMP_M && imp_kind != HOTRG_T_IMP_M1)
+        return set_err(ctx, HOTRG_EINVAL, "imp_kind must be PURE, IMP_M or IMP_M1");
+    hotrg_status first = HOTRG_OK;
+    std::vector<int> valid;
+    size_t need = 0;
+    for (int i = 0; i < npoints; ++i) {
+        memset(&out[i], 0, sizeof(hotrg_result));
+        hotrg_status s = check_params(ctx, &params[i]);
+        if (s == HOTRG_OK && (imp_kind != HOTRG_T_PURE) && params[i].tkind == HOTRG_T_ISING)
+            s = set_err(ctx, HOTRG_EINVAL, "no Ising impurity");
+        if (s != HOTRG_OK) {
+            out[i].status = s;
+            if (first == HOTRG_OK) first = s;
+            continue;
+        }
+        PointPlan pl;
+        point_bytes(&params[i], imp_kind, pl);
+        need = std::max(need, pl.bytes + 4096);
+        valid.push_back(i);
+    }
+    if (valid.empty()) return first;
+    // workers: own non-blocking stream and workspace each
+    Batch* B = (Batch*)ctx->batch;
+    if (B && (int)B->workers.size() != nstreams) {
+        batch_free(B);
+        B = nullptr;
+        ctx->batch = nullptr;
+    }
+    if (!B) {
+        B = new Batch();
+        ctx->batch = B;
+        for (int w = 0; w < nstreams; ++w) {
+            Worker wk;
+            HOTRG_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&wk.stream, cudaStreamNonBlocking));
+            wk.ctx = new hotrg_ctx();
+            wk.ctx->stream = wk.stream;
+            wk.ctx->device = ctx->device;
+            wk.ctx->sm_count = ctx->sm_count;
+            wk.ctx->smem_optin = ctx->smem_optin;
+            wk.ctx->tc_ok = ctx->tc_ok;
+            B->workers.push_back(wk);
+        }
+    }
+    for (Worker& w : B->workers)
+        if (w.ctx->ws.cap < need) {
+            for (auto& g : w.graphs) cudaGraphExecDestroy(g.exec);  // their buffers move
+            w.graphs.clear();
+            hotrg_status s = ws_reserve(w.ctx, need);
+            if (s != HOTRG_OK) return set_err(ctx, s, w.ctx->last_error);
+        }
+    // longest processing time first, each point to the least-loaded worker
+    std::vector<double> cost(npoints, 0.0);
+    for (int i : valid) cost[i] = point_cost(&params[i]);
+    std::sort(valid.begin(), valid.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int>> queue(nstreams);
+    std::vector<double> load(nstreams, 0.0);
+    for (int i : valid) {
+        int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        queue[w].push_back(i);
+        load[w] += cost[i];
+    }
+    // pinned staging: parameters in, scalars out
+    hotrg_params* hp = nullptr;
+    RunDev* hr = nullptr;
+    hotrg_step_info* hi = nullptr;
+    HOTRG_CUDA_TRY(ctx, cudaHostAlloc((void**)&hp, sizeof(hotrg_params) * npoints, cudaHostAllocDefault));
+    if (cudaHostAlloc((void**)&hr, sizeof(RunDev) * npoints, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&hi, sizeof(hotrg_step_info) * HOTRG_MAX_STEPS * npoints, cudaHostAllocDefault) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(hp);
+        if (hr) cudaFreeHost(hr);
+        return set_err(ctx, HOTRG_ENOMEM, "pinned staging");
+    }
+    std::vector<PointPlan> plans(npoints);
+    hotrg_status err = HOTRG_OK;
+    size_t rounds = 0;
+    for (auto& q : queue) rounds = std::max(rounds, q.size());
+    for (size_t r = 0; r < rounds && err == HOTRG_OK; ++r) {
+        for (int w = 0; w < nstreams && err == HOTRG_OK; ++w) {
+            if (r >= queue[w].size()) continue;
+            const int i = queue[w][r];
+            const hotrg_params* p = &params[i];
+            Worker& wk = B->workers[w];
+            hotrg_ctx* wc = wk.ctx;
+            hp[i] = *p;
+            const ClassKey key = class_of(p, imp_kind);
+            Worker::Graph* g = nullptr;
+            for (auto& gg : wk.graphs)
+                if (gg.key == key) g = &gg;
+            PointPlan& pl = plans[i];
+            hotrg_status s;
+            if (!g) {
+                // first point of this class on this worker: run it directly, then capture the class's graph
+                if ((s = plan_point(wc, p, imp_kind, pl, need)) != HOTRG_OK) {
+                    err = set_err(ctx, s, wc->last_error);
+                    break;
+                }
+                cudaMemcpyAsync(pl.dparams, &hp[i], sizeof(hotrg_params), cudaMemcpyHostToDevice, wk.stream);
+                if ((s = enqueue_point(wc, p, imp_kind, pl)) != HOTRG_OK) {
+                    err = set_err(ctx, s, wc->last_error);
+                    break;
+                }
+                Worker::Graph ng;
+                ng.key = key;
+                ng.plan = pl;
+                PointPlan cap;
+                plan_point(wc, p, imp_kind, cap, need);  // same carving as pl
+                const long long before = g_launches.load();
+                cudaGraph_t graph;
+                if (cudaStreamBeginCapture(wk.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    err = set_err(ctx, HOTRG_ECUDA, "cudaStreamBeginCapture failed");
+                    break;
+                }
+                s = enqueue_point(wc, p, imp_kind, cap);
+                const cudaError_t ce = cudaStreamEndCapture(wk.stream, &graph);
+                if (s != HOTRG_OK || ce != cudaSuccess) {
+                    cudaGetLastError();
+                    err = set_err(ctx, HOTRG_ECUDA, "graph capture failed: " + wc->last_error);
+                    break;
+                }
+                ng.launches = g_launches.load() - before;
+                g_launches.fetch_sub(ng.launches);  // captured, not launched
+                if (cudaGraphInstantiate(&ng.exec, graph, 0) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphDestroy(graph);
+                    err = set_err(ctx, HOTRG_ECUDA, "cudaGraphInstantiate failed");
+                    break;
+                }
+                cudaGraphDestroy(graph);
+                wk.graphs.push_back(ng);
+            } else {
+                pl = g->plan;
+                cudaMemcpyAsync(pl.dparams, &hp[i], sizeof(hotrg_params), cudaMemcpyHostToDevice, wk.stream);
+                if (cudaGraphLaunch(g->exec, wk.stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    err = set_err(ctx, HOTRG_ECUDA, "cudaGraphLaunch failed");
+                    break;
+                }
+                HOTRG_COUNT(g->launches);
+            }
+            cudaMemcpyAsync(&hr[i], pl.rd, sizeof(RunDev), cudaMemcpyDeviceToHost, wk.stream);
+            cudaMemcpyAsync(&hi[(size_t)i * HOTRG_MAX_STEPS], pl.infos, sizeof(hotrg_step_info) * p->n_steps,
+                            cudaMemcpyDeviceToHost, wk.stream);
+        }
+    }
+    for (Worker& w : B->workers) cudaStreamSynchronize(w.stream);
+    if (cudaGetLastError() != cudaSuccess && err == HOTRG_OK) err = set_err(ctx, HOTRG_ECUDA, "batch execution failed");
+    if (err == HOTRG_OK) {
+        hotrg_status us = umma_check_status(ctx);
+        if (us != HOTRG_OK) err = us;
+    }
+    for (int i : valid) {
+        if (err != HOTRG_OK) {
+            out[i].status = err;
+            continue;
+        }
+        memcpy(out[i].step, &hi[(size_t)i * HOTRG_MAX_STEPS], sizeof(hotrg_step_info) * params[i].n_steps);
+        hotrg_status s = unpack_point(ctx, &params[i], plans[i], hr[i], &out[i]);
+        if (s != HOTRG_OK && first == HOTRG_OK) first = s;
+    }
+    cudaFreeHost(hp);
+    cudaFreeHost(hr);
+    cudaFreeHost(hi);
+    return err != HOTRG_OK ? err : first;
 }
 
 hotrg_status hotrg_observables(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints, double hb,

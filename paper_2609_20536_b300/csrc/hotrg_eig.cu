@@ -427,12 +427,62 @@ __device__ void cgs2(T* Y, int m, int b, T* r, double* red, uint32_t salt, doubl
     }
 }
 
+// One-warp CGS2 on the b columns of Yt (stored transposed: column j is the
+// contiguous row Yt[j][0..m)), with the same replacement of numerically
+// dependent columns as cgs2().  Only warp-level synchronisation.
+__device__ void cgs2_warp_t(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* rbuf) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < b; ++j) {
+        float* yj = Yt + (int64_t)j * m;
+        bool done = false;
+        for (int attempt = 0; attempt < 4 && !done; ++attempt) {
+            if (attempt > 0) {
+                for (int t = lane; t < m; t += 32) yj[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)j);
+                __syncwarp();
+            }
+            float n0 = 0.f;
+            for (int t = lane; t < m; t += 32) n0 = fmaf(yj[t], yj[t], n0);
+            for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+            for (int pass = 0; pass < 2 && j > 0; ++pass) {
+                for (int i = 0; i < j; ++i) {
+                    const float* yi = Yt + (int64_t)i * m;
+                    float acc = 0.f;
+                    for (int t = lane; t < m; t += 32) acc = fmaf(yi[t], yj[t], acc);
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) rbuf[i] = acc;
+                }
+                __syncwarp();
+                for (int t = lane; t < m; t += 32) {
+                    float acc = yj[t];
+                    for (int i = 0; i < j; ++i) acc = fmaf(-rbuf[i], Yt[(int64_t)i * m + t], acc);
+                    yj[t] = acc;
+                }
+                __syncwarp();
+            }
+            float nrm = 0.f;
+            for (int t = lane; t < m; t += 32) nrm = fmaf(yj[t], yj[t], nrm);
+            for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+            if (nrm > dep_tol * dep_tol * n0 && nrm > 1e-30f) {
+                const float inv = rsqrtf(nrm);
+                for (int t = lane; t < m; t += 32) yj[t] *= inv;
+                done = true;
+            }
+            __syncwarp();
+        }
+        if (!done) {
+            for (int t = lane; t < m; t += 32) yj[t] = 0.f;
+            __syncwarp();
+        }
+    }
+}
+
+// FP32 block subspace iteration on one block: Qt, Yt are b x m (transposed);
+// the product Yt = (E_q Q)^T runs on all warps, the orthonormalisation on warp 0.
 __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double* EL, const double* ER, int n,
                                                                     int iters, EigWs w) {
     __shared__ float Es[32][65];
-    __shared__ float Qs[64][BCAP_MAX + 1];
+    __shared__ float Qs[BCAP_MAX][65];
     __shared__ float rbuf[BCAP_MAX];
-    __shared__ double red[40];
     const int side = blockIdx.y;
     const double* E = side == 0 ? EL : ER;
     const int nsec = *w.nsec;
@@ -452,12 +502,13 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
             E64[idx] = v;
             Ef[idx] = (float)v;
         }
-        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x)
-            Q[idx] = hash_unit((uint32_t)(idx / b), (uint32_t)(idx % b));
+        for (int64_t idx = threadIdx.x; idx < (int64_t)b * m; idx += blockDim.x)
+            Q[idx] = hash_unit((uint32_t)(idx % m), (uint32_t)(idx / m));
         __syncthreads();
-        cgs2<float>(Q, m, b, rbuf, red, 1u, 1e-3);
+        if (threadIdx.x < 32) cgs2_warp_t(Q, m, b, 1u, 1e-3f, rbuf);
+        __syncthreads();
         for (int it = 0; it < iters; ++it) {
-            // Y = Ef Q (m x b), tiled: 32 rows of Ef x 64 k per pass
+            // Yt[j][i] = sum_k Ef[i][k] Qt[j][k], tiles of 32 rows x 64 k
             for (int r0 = 0; r0 < m; r0 += 32) {
                 float acc[8];
 #pragma unroll
@@ -467,18 +518,19 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
                         const int i = idx / 64, k = idx % 64;
                         Es[i][k] = (r0 + i < m && k0 + k < m) ? Ef[(int64_t)(r0 + i) * m + k0 + k] : 0.f;
                     }
-                    for (int idx = threadIdx.x; idx < 64 * b; idx += blockDim.x) {
-                        const int k = idx / b, j = idx % b;
-                        Qs[k][j] = (k0 + k < m) ? Q[(int64_t)(k0 + k) * b + j] : 0.f;
+                    for (int idx = threadIdx.x; idx < b * 64; idx += blockDim.x) {
+                        const int j = idx / 64, k = idx % 64;
+                        Qs[j][k] = (k0 + k < m) ? Q[(int64_t)j * m + k0 + k] : 0.f;
                     }
                     __syncthreads();
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const int o = threadIdx.x + u * SUB_THREADS;  // output index inside the 32 x b tile
+                        const int o = threadIdx.x + u * SUB_THREADS;  // output (i, j) inside the 32 x b tile
                         if (o < 32 * b) {
-                            const int i = o / b, j = o % b;
+                            const int i = o % 32, j = o / 32;
                             float a = acc[u];
-                            for (int k = 0; k < 64; ++k) a = fmaf(Es[i][k], Qs[k][j], a);
+#pragma unroll 16
+                            for (int k = 0; k < 64; ++k) a = fmaf(Es[i][k], Qs[j][k], a);
                             acc[u] = a;
                         }
                     }
@@ -488,18 +540,19 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
                 for (int u = 0; u < 8; ++u) {
                     const int o = threadIdx.x + u * SUB_THREADS;
                     if (o < 32 * b) {
-                        const int i = o / b, j = o % b;
-                        if (r0 + i < m) Y[(int64_t)(r0 + i) * b + j] = acc[u];
+                        const int i = o % 32, j = o / 32;
+                        if (r0 + i < m) Y[(int64_t)j * m + r0 + i] = acc[u];
                     }
                 }
-                __syncthreads();
             }
-            cgs2<float>(Y, m, b, rbuf, red, 2u + 4u * (uint32_t)it, 1e-3);
+            __syncthreads();
+            if (threadIdx.x < 32) cgs2_warp_t(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, rbuf);
+            __syncthreads();
             float* t = Q;  // the orthonormal Y becomes the next Q
             Q = Y;
             Y = t;
         }
-        // leave the final basis in S1
+        // leave the final basis (b x m, transposed) in S1
         if (Q != (float*)(w.S1[side] + aoff)) {
             float* dst = (float*)(w.S1[side] + aoff);
             for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) dst[idx] = Q[idx];
@@ -521,7 +574,11 @@ __global__ void __launch_bounds__(SUB_THREADS) rr_prep_kernel(EigWs w) {
         const int64_t aoff = w.sec_aoff[sct];
         const float* Q32 = (const float*)(w.S1[side] + aoff);
         double* Q = w.S2[side] + aoff;
-        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) Q[idx] = (double)Q32[idx];
+        // Q32 is stored transposed (b x m)
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) {
+            const int t = (int)(idx / b), j = (int)(idx % b);
+            Q[idx] = (double)Q32[(int64_t)j * m + t];
+        }
         __syncthreads();
         cgs2<double>(Q, m, b, rbuf, red, 100003u, 1e-8);
     }
@@ -771,11 +828,11 @@ __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int dprime, double
 // ---------------------------------------------------------------------------
 // Side choice and projector P[(a,b)][j] (P must be zeroed beforehand).
 // ---------------------------------------------------------------------------
-__global__ void projector_kernel(int dprime, int policy, EigWs w, double* P, int32_t* q_out,
+__global__ void projector_kernel(int dprime, int policy, double side_rtol, EigWs w, double* P, int32_t* q_out,
                                  hotrg_step_info* info) {
     const double eL = *w.eps[0];
     const double eR = policy == 0 ? *w.eps[1] : nan("");
-    const int side = (policy == 0 && eR < eL * (1.0 - 1e-12)) ? 1 : 0;
+    const int side = (policy == 0 && eR < eL * (1.0 - side_rtol)) ? 1 : 0;
     const int j = blockIdx.x;
     const int slot = w.kept[side][j];
     const int sct = w.cand_sec[slot];
@@ -841,6 +898,7 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
     const bool exact = plan.exact || force_exact == 1;
     int small_thr = exact ? n : (bcap > 48 ? bcap : 48);
     if (!exact && thr_override) small_thr = thr_override;
+    const int hp0 = prof_begin(ctx);
     sectors_kernel<<<1, SORT_THREADS, MAX_N * 8, st>>>(q_h, plan.Dh, plan.sym, small_thr, bcap, w);
     HOTRG_COUNT(3);  // sectors, jacobi, select
     HOTRG_COUNT(exact ? 1 : 5);  // projector (+ subspace, rr_prep, rr_product, rr_finish)
@@ -850,10 +908,14 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
     jacobi_sectors_kernel<<<dim3(grid, sides), JAC_THREADS, JAC_SMEM_BYTES, st>>>(EL, ER, n, plan.max_sweeps,
                                                                                   plan.tol, w);
     HOTRG_LAUNCH_CHECK(ctx, "jacobi_sectors_kernel");
+    prof_end(ctx, hp0, PROF_EIG_PART0 + 0, 0.0);
     if (!exact) {
         const int sgrid = n < ctx->sm_count ? n : ctx->sm_count;
+        const int hp1 = prof_begin(ctx);
         subspace_fp32_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(EL, ER, n, sub_iters, w);
+        prof_end(ctx, hp1, PROF_EIG_PART0 + 1, 0.0);
         HOTRG_LAUNCH_CHECK(ctx, "subspace_fp32_kernel");
+        const int hp2 = prof_begin(ctx);
         rr_prep_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(w);
         HOTRG_LAUNCH_CHECK(ctx, "rr_prep_kernel");
         const int tiles = (n + GB_ROWS - 1) / GB_ROWS;
@@ -861,12 +923,15 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         HOTRG_LAUNCH_CHECK(ctx, "rr_product_kernel");
         rr_finish_kernel<<<dim3(sgrid, sides), JAC_THREADS, RR_SMEM_BYTES, st>>>(plan.max_sweeps, plan.tol, w);
         HOTRG_LAUNCH_CHECK(ctx, "rr_finish_kernel");
+        prof_end(ctx, hp2, PROF_EIG_PART0 + 2, 0.0);
     }
+    const int hp3 = prof_begin(ctx);
     select_kernel<<<sides, SORT_THREADS, MAX_N * 4 * 3, st>>>(plan.dprime, plan.tie_rtol, w);
     HOTRG_LAUNCH_CHECK(ctx, "select_kernel");
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(P, 0, (size_t)n * plan.dprime * sizeof(double), st));
-    projector_kernel<<<plan.dprime, 128, 0, st>>>(plan.dprime, plan.env_policy, w, P, q_out, info);
+    projector_kernel<<<plan.dprime, 128, 0, st>>>(plan.dprime, plan.env_policy, plan.side_rtol, w, P, q_out, info);
     HOTRG_LAUNCH_CHECK(ctx, "projector_kernel");
+    prof_end(ctx, hp3, PROF_EIG_PART0 + 3, 0.0);
     return HOTRG_OK;
 }
 

@@ -38,8 +38,9 @@ __device__ double bessel_in(int n, double x) {
 
 // a_n(beta, Delta) = sum_{m=-M..M} I_{n-2m}(beta Delta) I_m(beta (1 - Delta))   (Eq. 3.4)
 // F(Q) for the pure tensor (Eq. 3.15) and the impurities (Eq. 3.20, 3.21).
-__global__ void coeff_kernel(double beta, double delta, double h, double h1, int n_max, int m_range,
-                             int kind, double* a, double* F) {
+__global__ void coeff_kernel(const hotrg_params* __restrict__ dp, int n_max, int m_range, int kind, double* a,
+                             double* F) {
+    const double beta = dp->beta, delta = dp->delta, h = dp->h, h1 = dp->h1;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int na = 2 * n_max + 1;
     const int nf = 8 * n_max + 1;
@@ -86,7 +87,8 @@ __global__ void gxy_tensor_kernel(const double* a, const double* F, int n_max, i
 
 // 2D Ising: T[l,r,u,d] = sum_s W[s,l] W[s,r] W[s,u] W[s,d], W[s,0] = sqrt(cosh b),
 // W[s,1] = s sqrt(sinh b); each bond then carries exp(b s s').
-__global__ void ising_tensor_kernel(double beta, double* T, int32_t* labels) {
+__global__ void ising_tensor_kernel(const hotrg_params* __restrict__ dp, double* T, int32_t* labels) {
+    const double beta = dp->beta;
     const int i = threadIdx.x;
     if (i < 16) {
         const double w[2][2] = {{sqrt(cosh(beta)), sqrt(sinh(beta))}, {sqrt(cosh(beta)), -sqrt(sinh(beta))}};
@@ -98,10 +100,10 @@ __global__ void ising_tensor_kernel(double beta, double* T, int32_t* labels) {
     if (i < 2) labels[i] = i;
 }
 
-void launch_init_tensor(const hotrg_params* p, int kind, double* T, int32_t* labels, double* scratch,
-                        cudaStream_t st) {
+void launch_init_tensor(const hotrg_params* p, const hotrg_params* dp, int kind, double* T, int32_t* labels,
+                        double* scratch, cudaStream_t st) {
     if (kind == HOTRG_T_ISING) {
-        ising_tensor_kernel<<<1, 32, 0, st>>>(p->beta, T, labels);
+        ising_tensor_kernel<<<1, 32, 0, st>>>(dp, T, labels);
         HOTRG_COUNT(1);
         return;
     }
@@ -113,8 +115,7 @@ void launch_init_tensor(const hotrg_params* p, int kind, double* T, int32_t* lab
     int sym = SYM_U1;
     if (p->h != 0.0) sym = SYM_NONE;
     else if (p->h1 != 0.0) sym = SYM_Z2;
-    coeff_kernel<<<(na + nf + 127) / 128, 128, 0, st>>>(p->beta, p->delta, p->h, p->h1, n_max, m_range,
-                                                       kind, a, F);
+    coeff_kernel<<<(na + nf + 127) / 128, 128, 0, st>>>(dp, n_max, m_range, kind, a, F);
     const int total = na * na * na * na;
     gxy_tensor_kernel<<<(total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024, 256, 0, st>>>(
         a, F, n_max, sym, T, labels);

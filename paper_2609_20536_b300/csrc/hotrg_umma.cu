@@ -162,6 +162,88 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const void* __restrict_
     }
 }
 
+// Gather-slicer: the same slicing, reading element (r, k) of the operand at
+//   (r / (rd1 rd2)) rs0 + ((r / rd2) % rd1) rs1 + (r % rd2) rs2 + (k / kd) ks0 + (k % kd) ks1,
+// so that a permuted view of a tensor is sliced without materialising it.
+// Rows with K <= GATHER_SMEM_K are read once into shared memory (one warp per
+// row); longer rows are read twice.
+struct GatherMap {
+    int64_t rd1, rd2, rs0, rs1, rs2;
+    int64_t kd, ks0, ks1;
+};
+
+constexpr int GATHER_SMEM_K = 1024;  // rows up to this length are read once (8 KB of shared memory per warp)
+constexpr int GATHER_WARPS = 8;
+
+__device__ __forceinline__ int64_t gather_off(const GatherMap& g, int64_t r, int k) {
+    const int64_t r0 = r / (g.rd1 * g.rd2), r1 = (r / g.rd2) % g.rd1, r2 = r % g.rd2;
+    return r0 * g.rs0 + r1 * g.rs1 + r2 * g.rs2 + (int64_t)(k / g.kd) * g.ks0 + (int64_t)(k % g.kd) * g.ks1;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(32 * GATHER_WARPS) slice_gather_kernel(const void* __restrict__ X, GatherMap g,
+                                                                         int64_t rows, int K, int NS, int Kp,
+                                                                         __nv_bfloat16* __restrict__ out,
+                                                                         int64_t slice_stride,
+                                                                         int32_t* __restrict__ exps) {
+    extern __shared__ uint64_t srow_all[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * GATHER_WARPS + wib;
+    if (row >= rows) return;
+    const bool cached = K <= GATHER_SMEM_K;
+    uint64_t* srow = srow_all + (size_t)wib * GATHER_SMEM_K;
+    const int64_t rbase = gather_off(g, row, 0);
+    int emax = -2000;
+    for (int k = lane; k < K; k += 32) {
+        const int64_t off = rbase + (int64_t)(k / g.kd) * g.ks0 + (int64_t)(k % g.kd) * g.ks1;
+        const uint64_t bits = ((const uint64_t*)X)[off];
+        if (cached) srow[k] = bits;
+        const int ex = FMT == FMT_F64 ? exp_f64(__longlong_as_double((long long)bits))
+                                      : exp_f32(__uint_as_float((uint32_t)(bits & 0xffffffffu)));
+        emax = max(emax, ex);
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    __syncwarp();
+    const int e = emax <= -2000 ? 0 : emax + 1;
+    if (lane == 0) exps[row] = e;
+    const int T = SLICE_B1 + 8 * (NS - 1);
+    __nv_bfloat16* o0 = out + row * Kp;
+    for (int k = lane; k < Kp; k += 32) {
+        int64_t F = 0;
+        if (k < K && emax > -2000) {
+            uint64_t bits;
+            if (cached)
+                bits = srow[k];
+            else
+                bits = ((const uint64_t*)X)[rbase + (int64_t)(k / g.kd) * g.ks0 + (int64_t)(k % g.kd) * g.ks1];
+            if (FMT == FMT_F64) {
+                const double d = __longlong_as_double((long long)bits);
+                const int64_t a = (int64_t)fixed_f64(d, T - e);
+                F = d < 0.0 ? -a : a;
+            } else {
+                const float hi = __uint_as_float((uint32_t)(bits & 0xffffffffu));
+                const float lo = __uint_as_float((uint32_t)(bits >> 32));
+                const int G = 16;
+                const int64_t fh = (int64_t)fixed_f32(hi, T - e + G) * (hi < 0.f ? -1 : 1);
+                const int64_t fl = (int64_t)fixed_f32(lo, T - e + G) * (lo < 0.f ? -1 : 1);
+                F = (fh + fl + (1ll << (G - 1))) >> G;
+            }
+        }
+        int64_t r = F;
+        for (int p = 0; p < NS; ++p) {
+            const int sh = 8 * (NS - 1 - p);
+            int64_t c;
+            if (sh == 0) {
+                c = r;
+            } else {
+                c = (r + (1ll << (sh - 1))) >> sh;
+                r -= c << sh;
+            }
+            o0[p * slice_stride + k] = __float2bfloat16_rn(ldexpf((float)c, -8 * p));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // PTX helpers (tcgen05, TMA, mbarrier)
 // ---------------------------------------------------------------------------
@@ -653,6 +735,92 @@ hotrg_status umma_gemm_fmt(hotrg_ctx* ctx, int prec, int M, int N, int K, const 
     if (NS == 5) return launch_umma<5>(ctx, As, Bs, M, N, Kp, a);
     if (NS == 4) return launch_umma<4>(ctx, As, Bs, M, N, Kp, a);
     return launch_umma<3>(ctx, As, Bs, M, N, Kp, a);
+}
+
+static GatherMap plain_map(int64_t ld) {
+    GatherMap g;
+    g.rd1 = 1;
+    g.rd2 = 1;
+    g.rs0 = ld;
+    g.rs1 = 0;
+    g.rs2 = 0;
+    g.kd = 1 << 30;
+    g.ks0 = 0;
+    g.ks1 = 1;
+    return g;
+}
+
+// C = A B^T with A and B read through gather maps (both FP64 or FP32-pair).
+hotrg_status umma_gemm_gather(hotrg_ctx* ctx, int prec, int M, int N, int K, const void* A, const GatherMap& am,
+                              int afmt, const void* B, const GatherMap& bm, int bfmt, void* C, int cfmt, int64_t ldc,
+                              bool coarse) {
+    if (!ctx->tc_ok) return set_err(ctx, HOTRG_ENOTSUP, "tensor-core engine needs sm_103");
+    const int NS = ns_for(prec, coarse);
+    const int Kp = (int)round_up(K, BK);
+    const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
+    __nv_bfloat16* As = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * Mp * Kp * 2);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * Np * Kp * 2);
+    int32_t* eA = (int32_t*)ws_alloc(ctx, (size_t)Mp * 4);
+    int32_t* eB = (int32_t*)ws_alloc(ctx, (size_t)Np * 4);
+    if (!As || !Bs || !eA || !eB) return set_err(ctx, HOTRG_ENOMEM, "umma workspace exhausted");
+    int32_t* st = umma_status_word(ctx);
+    if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
+    static bool attr = false;
+    if (!attr) {
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_gather_kernel<FMT_F64>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 GATHER_WARPS * GATHER_SMEM_K * 8));
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_gather_kernel<FMT_F32PAIR>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 GATHER_WARPS * GATHER_SMEM_K * 8));
+        attr = true;
+    }
+    cudaStream_t s = ctx->stream;
+    const int smem = K <= GATHER_SMEM_K ? GATHER_WARPS * GATHER_SMEM_K * 8 : 0;
+    const int h_slice = prof_begin(ctx);
+    const int64_t gA = (M + GATHER_WARPS - 1) / GATHER_WARPS, gB = (N + GATHER_WARPS - 1) / GATHER_WARPS;
+    if (afmt == FMT_F64)
+        slice_gather_kernel<FMT_F64><<<(unsigned)gA, 32 * GATHER_WARPS, smem, s>>>(A, am, M, K, NS, Kp, As,
+                                                                                  (int64_t)M * Kp, eA);
+    else
+        slice_gather_kernel<FMT_F32PAIR><<<(unsigned)gA, 32 * GATHER_WARPS, smem, s>>>(A, am, M, K, NS, Kp, As,
+                                                                                      (int64_t)M * Kp, eA);
+    if (bfmt == FMT_F64)
+        slice_gather_kernel<FMT_F64><<<(unsigned)gB, 32 * GATHER_WARPS, smem, s>>>(B, bm, N, K, NS, Kp, Bs,
+                                                                                  (int64_t)N * Kp, eB);
+    else
+        slice_gather_kernel<FMT_F32PAIR><<<(unsigned)gB, 32 * GATHER_WARPS, smem, s>>>(B, bm, N, K, NS, Kp, Bs,
+                                                                                      (int64_t)N * Kp, eB);
+    HOTRG_COUNT(2);
+    prof_end(ctx, h_slice, PROF_SLICE, 0.0);
+    HOTRG_LAUNCH_CHECK(ctx, "slice_gather_kernel");
+    UmmaArgs a;
+    a.K = K;
+    a.prof_class = coarse ? PROF_GEMM_COARSE : PROF_GEMM_ENV;
+    a.M = M;
+    a.N = N;
+    a.Kp = Kp;
+    a.eA = eA;
+    a.eB = eB;
+    a.C = C;
+    a.ldc = ldc;
+    a.out_fmt = cfmt;
+    a.group_m = 16;
+    a.status = st;
+    if (NS == 5) return launch_umma<5>(ctx, As, Bs, M, N, Kp, a);
+    if (NS == 4) return launch_umma<4>(ctx, As, Bs, M, N, Kp, a);
+    return launch_umma<3>(ctx, As, Bs, M, N, Kp, a);
+}
+
+// Gathered contraction with FP64 operands and output, as used by one HOTRG step.
+hotrg_status umma_contract_gather(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, const int64_t* am,
+                                  const double* B, const int64_t* bm, double* C, int64_t ldc, bool coarse) {
+    GatherMap ga{am[0], am[1], am[2], am[3], am[4], am[5], am[6], am[7]};
+    GatherMap gb{bm[0], bm[1], bm[2], bm[3], bm[4], bm[5], bm[6], bm[7]};
+    const size_t mark = ctx->ws.used;
+    hotrg_status s = umma_gemm_gather(ctx, prec, M, N, K, A, ga, FMT_F64, B, gb, FMT_F64, C, FMT_F64, ldc, coarse);
+    ctx->ws.used = mark;
+    return s;
 }
 
 hotrg_status umma_gemm(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda, const double* B,

@@ -18,7 +18,7 @@ extern std::atomic<long long> g_launches;
 
 // profiling classes
 enum ProfClass : int { PROF_GEMM_ENV = 0, PROF_GEMM_COARSE = 1, PROF_GEMM_OTHER = 2, PROF_SLICE = 3, PROF_EIG = 4,
-                       PROF_STEP = 5 };
+                       PROF_STEP = 5, PROF_EIG_PART0 = 6 /* .. 9 */ };
 
 struct ProfMark {
     cudaEvent_t a, b;
@@ -55,6 +55,7 @@ struct hotrg_ctx {
     int smem_optin = 0;
     bool tc_ok = false;  // sm_103a tensor-core path usable on this device
     hotrg::Profiler prof;
+    void* batch = nullptr;  // worker streams and graph cache of hotrg_run_batch
 };
 
 namespace hotrg {
@@ -105,8 +106,10 @@ void launch_norm(const double* x, int64_t n, double* partial, double* norm, cuda
 void launch_scale_inv(double* x, int64_t n, const double* c, cudaStream_t st);
 // *tr = sum_{x,y} T[x][x][y][y] for T [Dx][Dx][Dy][Dy]
 void launch_trace(const double* T, int Dx, int Dy, double* tr, cudaStream_t st);
-// Initial tensor (Eq. 3.4, 3.15, 3.20, 3.21) or the Ising tensor.
-void launch_init_tensor(const hotrg_params* p, int kind, double* T, int32_t* labels,
+// Initial tensor (Eq. 3.4, 3.15, 3.20, 3.21) or the Ising tensor.  Sizes and the
+// symmetry come from the host copy p; beta, Delta, h, h1 are read on the
+// device from dp (so a captured graph can be replayed with new values).
+void launch_init_tensor(const hotrg_params* p, const hotrg_params* dp, int kind, double* T, int32_t* labels,
                         double* scratch, cudaStream_t st);
 // Step bookkeeping: info->ln_c = log(*norm), lnz accumulation etc.
 void launch_step_scalars(const double* norm, hotrg_step_info* info, double* lnz_acc, double weight,
@@ -122,6 +125,7 @@ struct EigPlan {
     int max_sweeps;
     double tol;
     double tie_rtol;
+    double side_rtol;
     int env_policy;
     bool exact;   // FP64 Jacobi on every block (the FP64 form)
 };
@@ -141,5 +145,10 @@ size_t gemm_engine_workspace(int prec, int64_t M, int64_t N, int64_t K);
 hotrg_status umma_contract(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, int64_t lda,
                            const double* B, int64_t ldb, double* C, int64_t ldc);
 hotrg_status umma_check_status(hotrg_ctx* ctx);
+// Split-form contraction reading A and B through gather maps
+// {rd1, rd2, rs0, rs1, rs2, kd, ks0, ks1}: element (r, k) sits at
+// (r/(rd1 rd2)) rs0 + ((r/rd2) % rd1) rs1 + (r % rd2) rs2 + (k/kd) ks0 + (k % kd) ks1.
+hotrg_status umma_contract_gather(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, const int64_t* am,
+                                  const double* B, const int64_t* bm, double* C, int64_t ldc, bool coarse);
 
 }  // namespace hotrg

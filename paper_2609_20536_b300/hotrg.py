@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
         ("n_max", ctypes.c_int32), ("d_cut", ctypes.c_int32), ("n_steps", ctypes.c_int32),
         ("prec", ctypes.c_int32), ("env_policy", ctypes.c_int32), ("m_range", ctypes.c_int32),
         ("eig_max_sweeps", ctypes.c_int32), ("tkind", ctypes.c_int32),
-        ("tie_rtol", ctypes.c_double), ("eig_tol", ctypes.c_double),
+        ("tie_rtol", ctypes.c_double), ("eig_tol", ctypes.c_double), ("side_rtol", ctypes.c_double),
     ]
 
 
@@ -58,7 +58,7 @@ class Profile(ctypes.Structure):
     _fields_ = [
         ("launches", ctypes.c_int64), ("gemm_calls", ctypes.c_int64 * 3), ("gemm_ms", ctypes.c_double * 3),
         ("gemm_flops", ctypes.c_double * 3), ("slice_ms", ctypes.c_double), ("eig_ms", ctypes.c_double),
-        ("step_ms", ctypes.c_double), ("steps", ctypes.c_int64),
+        ("step_ms", ctypes.c_double), ("steps", ctypes.c_int64), ("eig_part_ms", ctypes.c_double * 4),
     ]
 
 
@@ -106,9 +106,9 @@ lib = _load()
 
 
 def params(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, prec=FP64, env_policy=0, m_range=50,
-           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0):
+           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0, side_rtol=0.0):
     return Params(beta, delta, h, h1, n_max, d_cut, n_steps, prec, env_policy, m_range,
-                  eig_max_sweeps, tkind, tie_rtol, eig_tol)
+                  eig_max_sweeps, tkind, tie_rtol, eig_tol, side_rtol)
 
 
 def hotrg_create(workspace_bytes=0, stream=0):
@@ -157,6 +157,20 @@ def hotrg_run(ctx, plist, imp_kind=T_PURE, check=True):
     return list(out)
 
 
+def hotrg_run_batch(ctx, plist, imp_kind=T_PURE, nstreams=2, check=True):
+    n = len(plist)
+    arr = (Params * n)(*plist)
+    out = (Result * n)()
+    f = lib.hotrg_run_batch
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                  ctypes.POINTER(Result)]
+    f.restype = ctypes.c_int
+    st = f(ctx, arr, n, imp_kind, nstreams, out)
+    if check:
+        _check(ctx, st)
+    return list(out)
+
+
 def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
     n = len(plist)
     arr = (Params * n)(*plist)
@@ -190,6 +204,96 @@ def hotrg_contract_noalloc(prec, M, N, K, A, lda, B, ldb, C, ldc, stream=0):
              ctypes.c_void_p(stream or None))
 
 
+class MLP:
+    """Ensemble of 2-128-128-128-4 networks (libhotrg surrogate kernels)."""
+
+    def __init__(self, ensemble=4, seed=20536, stream=0):
+        f = lib.hotrg_mlp_create
+        f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p]
+        f.restype = ctypes.c_int
+        lib.hotrg_mlp_destroy.argtypes = [ctypes.c_void_p]
+        lib.hotrg_mlp_destroy.restype = None
+        lib.hotrg_mlp_num_params.restype = ctypes.c_int64
+        self.handle = ctypes.c_void_p()
+        st = f(ctypes.byref(self.handle), ensemble, seed, ctypes.c_void_p(stream or None))
+        if st != OK:
+            raise HotrgError(st, "hotrg_mlp_create failed")
+        self.ensemble = ensemble
+        self.nparams = lib.hotrg_mlp_num_params()
+
+    def close(self):
+        if self.handle:
+            lib.hotrg_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _f32(a):
+        import numpy as np
+        return np.ascontiguousarray(a, dtype=np.float32)
+
+    def _ptr(self, a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+    def set_params(self, member, flat):
+        a = self._f32(flat)
+        lib.hotrg_mlp_set_params.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+        st = lib.hotrg_mlp_set_params(self.handle, member, self._ptr(a))
+        if st != OK:
+            raise HotrgError(st, "hotrg_mlp_set_params")
+
+    def get_params(self, member):
+        import numpy as np
+        a = np.zeros(self.nparams, dtype=np.float32)
+        lib.hotrg_mlp_get_params.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
+        st = lib.hotrg_mlp_get_params(self.handle, member, self._ptr(a))
+        if st != OK:
+            raise HotrgError(st, "hotrg_mlp_get_params")
+        return a
+
+    def gradients(self, member, X, T):
+        import numpy as np
+        X, T = self._f32(X), self._f32(T)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float()
+        f = lib.hotrg_mlp_gradients
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                      ctypes.c_int32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+        st = f(self.handle, member, self._ptr(X), self._ptr(T), len(X), ctypes.byref(loss), self._ptr(g))
+        if st != OK:
+            raise HotrgError(st, "hotrg_mlp_gradients")
+        return loss.value, g
+
+    def train(self, X, T, epochs=100, batch=256, lr=1e-3):
+        X, T = self._f32(X), self._f32(T)
+        loss = ctypes.c_float()
+        f = lib.hotrg_mlp_train
+        f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
+                      ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+        st = f(self.handle, self._ptr(X), self._ptr(T), len(X), epochs, batch, lr, ctypes.byref(loss))
+        if st != OK:
+            raise HotrgError(st, "hotrg_mlp_train")
+        return loss.value
+
+    def predict(self, X):
+        import numpy as np
+        X = self._f32(X)
+        mean = np.zeros((len(X), 4), dtype=np.float32)
+        spread = np.zeros((len(X), 4), dtype=np.float32)
+        f = lib.hotrg_mlp_predict
+        f.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int32, ctypes.POINTER(ctypes.c_float),
+                      ctypes.POINTER(ctypes.c_float)]
+        st = f(self.handle, self._ptr(X), len(X), self._ptr(mean), self._ptr(spread))
+        if st != OK:
+            raise HotrgError(st, "hotrg_mlp_predict")
+        return mean, spread
+
+
 class Context:
     """Owns one hotrg_ctx bound to a CUDA stream (0: legacy default)."""
 
@@ -215,6 +319,9 @@ class Context:
 
     def run(self, plist, imp_kind=T_PURE):
         return hotrg_run(self.handle, plist, imp_kind)
+
+    def run_batch(self, plist, imp_kind=T_PURE, nstreams=2):
+        return hotrg_run_batch(self.handle, plist, imp_kind, nstreams)
 
     def observables(self, plist, hb=1e-3, hbar=0.01, dh=1e-3):
         return hotrg_observables(self.handle, plist, hb, hbar, dh)

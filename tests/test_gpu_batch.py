@@ -1,0 +1,60 @@
+"""hotrg_run_batch: points of several classes on several worker streams, the
+first point of each class run directly and the rest replayed from a captured
+CUDA graph.  The kernels and their inputs are the same as hotrg_run's, so the
+results must be bitwise identical; a few are also checked against the oracle."""
+import pytest
+
+from oracle import hotrg as OH
+
+from parity_points import BATCH, BATCH_ORACLE
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2609_20536_b300 import build
+    build.build()
+    from paper_2609_20536_b300 import hotrg
+    return hotrg
+
+
+@pytest.fixture(scope="module")
+def C(H):
+    c = H.Context()
+    yield c
+    c.close()
+
+
+def points(H, prec):
+    return [H.params(*pt, prec=prec) for pt in BATCH]
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "SPLIT_BF16"])
+@pytest.mark.parametrize("nstreams", [1, 3])
+def test_batch_equals_single_runs(H, C, prec_name, nstreams):
+    prec = getattr(H, prec_name)
+    pts = points(H, prec)
+    single = [C.run([p])[0].lnz_per_site for p in pts]
+    for repeat in range(2):  # the second call replays graphs only
+        got = C.run_batch(pts, nstreams=nstreams)
+        assert [r.status for r in got] == [0] * len(pts)
+        assert [r.lnz_per_site for r in got] == single
+        for r, p in zip(got, pts):
+            assert r.n_steps == p.n_steps and r.step[p.n_steps - 1].dprime > 0
+
+
+def test_batch_against_oracle(H, C):
+    pts = [H.params(*pt, prec=H.SPLIT_BF16) for pt in BATCH_ORACLE]
+    got = C.run_batch(pts, nstreams=2)
+    for r, p in zip(got, pts):
+        ref = OH.run_gxy(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps).lnz_per_site
+        assert abs(r.lnz_per_site - ref) < 1e-9
+
+
+def test_batch_with_invalid_entries(H, C):
+    pts = points(H, H.SPLIT_BF16)[:3]
+    pts.insert(1, H.params(-1.0, 0.5, 2, 12, 14))
+    got = H.hotrg_run_batch(C.handle, pts, nstreams=2, check=False)
+    assert got[1].status == H.EINVAL
+    assert all(got[i].status == 0 for i in (0, 2, 3))

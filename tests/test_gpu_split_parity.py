@@ -8,6 +8,8 @@ import pytest
 from oracle import gxy
 from oracle import hotrg as OH
 
+from parity_points import SPLIT_SHAPES
+
 pytestmark = pytest.mark.gpu
 
 
@@ -26,9 +28,7 @@ def C(H):
     c.close()
 
 
-@pytest.mark.parametrize("beta,delta,nm,dcut,steps", [
-    (1.0, 0.5, 2, 16, 20), (1.6, 0.3, 4, 16, 25), (0.7, 0.8, 4, 24, 14), (1.2, 0.1, 3, 13, 12), (2.0, 0.9, 4, 16, 25),
-])
+@pytest.mark.parametrize("beta,delta,nm,dcut,steps", SPLIT_SHAPES)
 def test_split_bf16_lnz(H, C, beta, delta, nm, dcut, steps):
     ref = OH.run_gxy(beta, delta, nm, dcut, steps)
     res = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16)])[0]
