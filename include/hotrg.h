@@ -199,6 +199,16 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
 hotrg_status hotrg_observables(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
                                double hb, double hbar, double dh, hotrg_obs* out);
 
+/* hotrg_observables for many points at once: the nine runs of every point
+ * (beta, beta +- hb; h = hbar, hbar +- dh with the M impurity; h1 = hbar,
+ * hbar +- dh with the M1 impurity) go through hotrg_run_batch on nstreams
+ * worker streams (1..16), so the outputs equal hotrg_observables' bit for
+ * bit.  Synchronous.  Returns the first failing run's status (each out[i]
+ * holds its own); HOTRG_EINVAL for bad arguments. */
+hotrg_status hotrg_observables_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
+                                     double hb, double hbar, double dh, int32_t nstreams,
+                                     hotrg_obs* out);
+
 /* Verification entry point for the contraction engine of a precision
  * form: C = A B^T with A (device, M x K FP64, row stride lda), B (device,
  * N x K FP64, row stride ldb), C (device, M x N FP64, row stride ldc).
@@ -267,6 +277,52 @@ hotrg_status hotrg_mlp_train(hotrg_mlp* m, const float* X, const float* T, int32
                              int32_t batch, float lr, float* final_loss);
 /* Ensemble mean and spread (standard deviation over members) per output. */
 hotrg_status hotrg_mlp_predict(hotrg_mlp* m, const float* X, int32_t n, float* mean, float* spread);
+
+/* Surrogate driver (no counterpart in the thesis).  The surrogate maps
+ * (beta, Delta) to (f, C_V, chi, chi1) = (f, cv, chi, chi1) of hotrg_obs,
+ * through the MLP ensemble above on standardised inputs and outputs.  X
+ * arrays are host n x 2 (beta, Delta) and Y arrays host n x 4, row-major,
+ * FP64, in physical units. */
+typedef struct {
+    double x_mean[2], x_std[2];   /* input standardisation, x' = (x - mean) / std */
+    double y_mean[4], y_std[4];   /* output standardisation */
+} hotrg_scaling;
+
+/* Mean and population standard deviation of every column (a zero standard
+ * deviation is replaced by 1).  Host only.  Errors: HOTRG_EINVAL. */
+hotrg_status hotrg_scaling_fit(const double* X, const double* Y, int32_t n, hotrg_scaling* s);
+
+/* Fit the scaling to (X, Y) and train every member of m on the
+ * standardised data (hotrg_mlp_train).  Synchronous. */
+hotrg_status hotrg_surrogate_fit(hotrg_mlp* m, const double* X, const double* Y, int32_t n, int32_t epochs,
+                                 int32_t batch, float lr, hotrg_scaling* s, float* final_loss);
+
+/* Ensemble prediction in physical units (y, n x 4) and the ensemble spread
+ * in standardised units (spread, n x 4; may be NULL).  Synchronous. */
+hotrg_status hotrg_surrogate_predict(hotrg_mlp* m, const hotrg_scaling* s, const double* X, int32_t n,
+                                     double* y, double* spread);
+
+/* Refinement points near the transition: for each of n_delta values of
+ * Delta, the surrogate's C_V and chi are evaluated on n_beta points evenly
+ * spaced over [beta_lo, beta_hi]; around each of the two maxima, per_peak
+ * points evenly spaced over [beta* - width, beta* + width] (clipped to the
+ * range) are written to X_out (n_delta * 2 * per_peak rows: Delta-major,
+ * C_V window first).  peaks_out (n_delta x 2, may be NULL) receives the
+ * beta of the C_V and chi maxima.  Synchronous. */
+hotrg_status hotrg_surrogate_peaks(hotrg_mlp* m, const hotrg_scaling* s, const double* deltas, int32_t n_delta,
+                                   double beta_lo, double beta_hi, int32_t n_beta, int32_t per_peak,
+                                   double width, double* X_out, double* peaks_out);
+
+/* Predict at n points; every point whose largest standardised spread
+ * exceeds threshold is re-solved by hotrg_observables_batch with params
+ * base (beta and Delta replaced; nstreams worker streams) and its y row
+ * replaced by the HOTRG values.  solved[i] = 1 for re-solved points, else
+ * 0; *n_solved (may be NULL) counts them.  spread (may be NULL) keeps the
+ * ensemble's spread for every point.  Synchronous. */
+hotrg_status hotrg_surrogate_refine(hotrg_ctx* ctx, hotrg_mlp* m, const hotrg_scaling* s,
+                                    const hotrg_params* base, const double* X, int32_t n, double threshold,
+                                    double hb, double hbar, double dh, int32_t nstreams, double* y,
+                                    double* spread, int32_t* solved, int32_t* n_solved);
 
 /* Per-kernel-class timing recorded with CUDA events on the context's stream
  * (the stream every library kernel runs on).  Classes of the contraction

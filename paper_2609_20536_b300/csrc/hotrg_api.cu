@@ -1025,4 +1025,68 @@ hotrg_status hotrg_observables(hotrg_ctx* ctx, const hotrg_params* params, int32
     return first;
 }
 
+
+hotrg_status hotrg_observables_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints, double hb,
+                                     double hbar, double dh, int32_t nstreams, hotrg_obs* out) {
+    if (!ctx) return HOTRG_EINVAL;
+    ctx->last_error.clear();
+    if (!params || !out || npoints < 0 || !(hb > 0) || !(hbar >= 0) || !(dh > 0) || hbar - dh < 0)
+        return set_err(ctx, HOTRG_EINVAL, "bad arguments (need hb > 0, dh > 0, hbar >= dh)");
+    if (nstreams < 1 || nstreams > 16) return set_err(ctx, HOTRG_EINVAL, "nstreams must lie in [1, 16]");
+    for (int i = 0; i < npoints; ++i) memset(&out[i], 0, sizeof(hotrg_obs));
+    if (npoints == 0) return HOTRG_OK;
+    // three families (beta +-hb pure; h = hbar +-dh with the M impurity; h1 = hbar +-dh with the M1
+    // impurity), three runs per point each, in the order (centre, +, -) of hotrg_observables
+    std::vector<hotrg_params> pp((size_t)3 * npoints);
+    std::vector<hotrg_result> rr((size_t)3 * npoints);
+    const int kinds[3] = {HOTRG_T_PURE, HOTRG_T_IMP_M, HOTRG_T_IMP_M1};
+    hotrg_status fatal = HOTRG_OK;
+    std::string fatal_msg;
+    for (int f = 0; f < 3; ++f) {
+        for (int i = 0; i < npoints; ++i) {
+            hotrg_params q = params[i];
+            q.h = 0.0;
+            q.h1 = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                hotrg_params a = q;
+                if (f == 0) a.beta = j == 0 ? q.beta : (j == 1 ? q.beta + hb : q.beta - hb);
+                if (f == 1) a.h = j == 0 ? hbar : (j == 1 ? hbar + dh : hbar - dh);
+                if (f == 2) a.h1 = j == 0 ? hbar : (j == 1 ? hbar + dh : hbar - dh);
+                pp[(size_t)3 * i + j] = a;
+            }
+        }
+        const hotrg_status s = hotrg_run_batch(ctx, pp.data(), 3 * npoints, kinds[f], nstreams, rr.data());
+        (void)s;  // per-run statuses are in rr
+        for (int i = 0; i < npoints; ++i) {
+            hotrg_obs& o = out[i];
+            const hotrg_result* r = &rr[(size_t)3 * i];
+            hotrg_status ps = HOTRG_OK;
+            for (int j = 0; j < 3 && ps == HOTRG_OK; ++j) ps = (hotrg_status)r[j].status;
+            if (ps != HOTRG_OK) {
+                if (o.status == HOTRG_OK) o.status = ps;
+                if (fatal == HOTRG_OK) {
+                    fatal = ps;
+                    fatal_msg = ctx->last_error;
+                }
+                continue;
+            }
+            if (o.status != HOTRG_OK) continue;
+            if (f == 0) {
+                o.lnz = r[0].lnz_per_site;
+                o.f = -o.lnz / params[i].beta;
+                o.cv = params[i].beta * params[i].beta *
+                       (r[1].lnz_per_site - 2.0 * r[0].lnz_per_site + r[2].lnz_per_site) / (hb * hb);
+            } else if (f == 1) {
+                o.m = r[0].imp_ratio;
+                o.chi = (r[1].imp_ratio - r[2].imp_ratio) / (2.0 * dh);
+            } else {
+                o.m1 = r[0].imp_ratio;
+                o.chi1 = (r[1].imp_ratio - r[2].imp_ratio) / (2.0 * dh);
+            }
+        }
+    }
+    if (fatal != HOTRG_OK) ctx->last_error = fatal_msg;
+    return fatal;
+}
+
 }  // extern "C"

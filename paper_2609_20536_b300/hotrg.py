@@ -70,6 +70,13 @@ class Obs(ctypes.Structure):
     ]
 
 
+class Scaling(ctypes.Structure):
+    _fields_ = [
+        ("x_mean", ctypes.c_double * 2), ("x_std", ctypes.c_double * 2),
+        ("y_mean", ctypes.c_double * 4), ("y_std", ctypes.c_double * 4),
+    ]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libhotrg.so not built ({LIB_PATH}); run paper_2609_20536_b300.build.build()")
@@ -92,6 +99,23 @@ def _load():
     lib.hotrg_run.restype = ctypes.c_int
     lib.hotrg_observables.argtypes = [vp, ctypes.POINTER(Params), i32, f64, f64, f64, ctypes.POINTER(Obs)]
     lib.hotrg_observables.restype = ctypes.c_int
+    lib.hotrg_observables_batch.argtypes = [vp, ctypes.POINTER(Params), i32, f64, f64, f64, i32,
+                                            ctypes.POINTER(Obs)]
+    lib.hotrg_observables_batch.restype = ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib.hotrg_scaling_fit.argtypes = [dp, dp, i32, ctypes.POINTER(Scaling)]
+    lib.hotrg_scaling_fit.restype = ctypes.c_int
+    lib.hotrg_surrogate_fit.argtypes = [vp, dp, dp, i32, i32, i32, ctypes.c_float, ctypes.POINTER(Scaling),
+                                        ctypes.POINTER(ctypes.c_float)]
+    lib.hotrg_surrogate_fit.restype = ctypes.c_int
+    lib.hotrg_surrogate_predict.argtypes = [vp, ctypes.POINTER(Scaling), dp, i32, dp, dp]
+    lib.hotrg_surrogate_predict.restype = ctypes.c_int
+    lib.hotrg_surrogate_peaks.argtypes = [vp, ctypes.POINTER(Scaling), dp, i32, f64, f64, i32, i32, f64, dp, dp]
+    lib.hotrg_surrogate_peaks.restype = ctypes.c_int
+    lib.hotrg_surrogate_refine.argtypes = [vp, vp, ctypes.POINTER(Scaling), ctypes.POINTER(Params), dp, i32, f64,
+                                           f64, f64, f64, i32, dp, dp, ip, ip]
+    lib.hotrg_surrogate_refine.restype = ctypes.c_int
     lib.hotrg_contract.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.c_int64, vp, ctypes.c_int64, vp,
                                    ctypes.c_int64]
     lib.hotrg_contract.restype = ctypes.c_int
@@ -177,6 +201,33 @@ def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
     out = (Obs * n)()
     _check(ctx, lib.hotrg_observables(ctx, arr, n, hb, hbar, dh, out))
     return list(out)
+
+
+def hotrg_observables_batch(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3, nstreams=2, check=True):
+    n = len(plist)
+    arr = (Params * n)(*plist)
+    out = (Obs * n)()
+    st = lib.hotrg_observables_batch(ctx, arr, n, hb, hbar, dh, nstreams, out)
+    if check:
+        _check(ctx, st)
+    return list(out)
+
+
+def _f64(a, cols):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, cols)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def hotrg_scaling_fit(X, Y):
+    """Column means and standard deviations (host C++; no device work)."""
+    X, xp = _f64(X, 2)
+    Y, yp = _f64(Y, 4)
+    s = Scaling()
+    st = lib.hotrg_scaling_fit(xp, yp, len(X), ctypes.byref(s))
+    if st != OK:
+        raise HotrgError(st, "hotrg_scaling_fit")
+    return s
 
 
 def hotrg_contract(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc):
@@ -294,6 +345,71 @@ class MLP:
         return mean, spread
 
 
+class Surrogate:
+    """MLP ensemble plus its standardisation: fit, predict, refinement
+    points near the C_V / chi maxima, and HOTRG re-solves of uncertain
+    points (hotrg_surrogate_* entry points)."""
+
+    def __init__(self, ensemble=4, seed=20536, stream=0):
+        self.mlp = MLP(ensemble, seed, stream)
+        self.scaling = None
+
+    def close(self):
+        self.mlp.close()
+
+    def fit(self, X, Y, epochs=200, batch=256, lr=1e-3):
+        X, xp = _f64(X, 2)
+        Y, yp = _f64(Y, 4)
+        self.scaling = Scaling()
+        loss = ctypes.c_float()
+        st = lib.hotrg_surrogate_fit(self.mlp.handle, xp, yp, len(X), epochs, batch, lr, ctypes.byref(self.scaling),
+                                     ctypes.byref(loss))
+        if st != OK:
+            raise HotrgError(st, "hotrg_surrogate_fit")
+        return loss.value
+
+    def predict(self, X):
+        import numpy as np
+        X, xp = _f64(X, 2)
+        y = np.zeros((len(X), 4))
+        sd = np.zeros((len(X), 4))
+        st = lib.hotrg_surrogate_predict(self.mlp.handle, ctypes.byref(self.scaling), xp, len(X),
+                                         y.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         sd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if st != OK:
+            raise HotrgError(st, "hotrg_surrogate_predict")
+        return y, sd
+
+    def peaks(self, deltas, beta_lo, beta_hi, n_beta, per_peak, width):
+        import numpy as np
+        d, dptr = _f64(deltas, 1)
+        X = np.zeros((len(d) * 2 * per_peak, 2))
+        pk = np.zeros((len(d), 2))
+        st = lib.hotrg_surrogate_peaks(self.mlp.handle, ctypes.byref(self.scaling), dptr, len(d), beta_lo, beta_hi,
+                                       n_beta, per_peak, width, X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       pk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if st != OK:
+            raise HotrgError(st, "hotrg_surrogate_peaks")
+        return X, pk
+
+    def refine(self, ctx, base, X, threshold=1e-3, hb=1e-3, hbar=0.01, dh=1e-3, nstreams=2):
+        import numpy as np
+        X, xp = _f64(X, 2)
+        n = len(X)
+        y = np.zeros((n, 4))
+        sd = np.zeros((n, 4))
+        solved = np.zeros(n, dtype=np.int32)
+        ns = ctypes.c_int32(0)
+        dptr = ctypes.POINTER(ctypes.c_double)
+        st = lib.hotrg_surrogate_refine(ctx.handle if isinstance(ctx, Context) else ctx, self.mlp.handle,
+                                        ctypes.byref(self.scaling), ctypes.byref(base), xp, n, threshold, hb, hbar,
+                                        dh, nstreams, y.ctypes.data_as(dptr), sd.ctypes.data_as(dptr),
+                                        solved.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(ns))
+        if st != OK:
+            raise HotrgError(st, "hotrg_surrogate_refine")
+        return y, sd, solved.astype(bool)
+
+
 class Context:
     """Owns one hotrg_ctx bound to a CUDA stream (0: legacy default)."""
 
@@ -325,3 +441,6 @@ class Context:
 
     def observables(self, plist, hb=1e-3, hbar=0.01, dh=1e-3):
         return hotrg_observables(self.handle, plist, hb, hbar, dh)
+
+    def observables_batch(self, plist, hb=1e-3, hbar=0.01, dh=1e-3, nstreams=2):
+        return hotrg_observables_batch(self.handle, plist, hb, hbar, dh, nstreams)

@@ -47,8 +47,9 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "hotrg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(hotrg_params), sizeof(hotrg_step_info), sizeof(hotrg_result),
-         sizeof(hotrg_obs), offsetof(hotrg_result, step), offsetof(hotrg_params, tie_rtol));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(hotrg_params), sizeof(hotrg_step_info), sizeof(hotrg_result),
+         sizeof(hotrg_obs), offsetof(hotrg_result, step), offsetof(hotrg_params, tie_rtol),
+         sizeof(hotrg_scaling), offsetof(hotrg_scaling, y_std));
   return 0;
 }
 '''
@@ -59,7 +60,8 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = list(map(int, subprocess.check_output([exe]).split()))
     assert got == [ctypes.sizeof(H.Params), ctypes.sizeof(H.StepInfo), ctypes.sizeof(H.Result),
-                   ctypes.sizeof(H.Obs), H.Result.step.offset, H.Params.tie_rtol.offset]
+                   ctypes.sizeof(H.Obs), H.Result.step.offset, H.Params.tie_rtol.offset,
+                   ctypes.sizeof(H.Scaling), H.Scaling.y_std.offset]
 
 
 def test_no_device_call_without_gpu(lib):
