@@ -185,6 +185,11 @@ hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoin
  * zero pattern -- of h, h1) on a worker runs directly; its sequence of
  * kernels is then captured once into a CUDA graph that later points of the
  * class replay, with beta, Delta, h, h1 fed through a device parameter slot.
+ * The workers start after the work already enqueued on the context's stream
+ * and the context's stream waits for all of them at the end, so CUDA events
+ * recorded on it bracket the batch.  With profiling on (hotrg_profile_enable)
+ * no graph is replayed: every point runs directly, its regions are timed on
+ * its worker's stream and added to the context's counters.
  * params, out: host arrays of npoints.  Synchronous.  Returns the first
  * non-OK status (each out[i].status holds its own). */
 hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,

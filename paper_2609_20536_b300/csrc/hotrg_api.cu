@@ -612,6 +612,7 @@ static double point_cost(const hotrg_params* p) {
 struct Worker {
     hotrg_ctx* ctx = nullptr;
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;  // joins the worker back into the context's stream
     struct Graph {
         ClassKey key;
         cudaGraphExec_t exec;
@@ -623,8 +624,22 @@ struct Worker {
 
 struct Batch {
     std::vector<Worker> workers;
+    cudaEvent_t fork = nullptr;  // workers start after the work already on the context's stream
     size_t reserve = 0;
 };
+
+static void profile_add(hotrg_profile& a, const hotrg_profile& b) {
+    for (int c = 0; c < 3; ++c) {
+        a.gemm_calls[c] += b.gemm_calls[c];
+        a.gemm_ms[c] += b.gemm_ms[c];
+        a.gemm_flops[c] += b.gemm_flops[c];
+    }
+    a.slice_ms += b.slice_ms;
+    a.eig_ms += b.eig_ms;
+    a.step_ms += b.step_ms;
+    a.steps += b.steps;
+    for (int c = 0; c < 4; ++c) a.eig_part_ms[c] += b.eig_part_ms[c];
+}
 
 static void batch_free(Batch* b) {
     if (!b) return;
@@ -636,8 +651,10 @@ static void batch_free(Batch* b) {
             for (cudaEvent_t e : w.ctx->prof.pool) cudaEventDestroy(e);
             delete w.ctx;
         }
+        if (w.done) cudaEventDestroy(w.done);
         if (w.stream) cudaStreamDestroy(w.stream);
     }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -838,8 +855,18 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
             wk.ctx->sm_count = ctx->sm_count;
             wk.ctx->smem_optin = ctx->smem_optin;
             wk.ctx->tc_ok = ctx->tc_ok;
+            HOTRG_CUDA_TRY(ctx, cudaEventCreateWithFlags(&wk.done, cudaEventDisableTiming));
             B->workers.push_back(wk);
         }
+        HOTRG_CUDA_TRY(ctx, cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+    }
+    // fork: every worker stream waits for the context stream's earlier work; with profiling on,
+    // points run directly (no graph replay) so that every region is timed on its worker stream
+    const bool profiling = ctx->prof.on;
+    HOTRG_CUDA_TRY(ctx, cudaEventRecord(B->fork, ctx->stream));
+    for (Worker& w : B->workers) {
+        w.ctx->prof.on = profiling;
+        HOTRG_CUDA_TRY(ctx, cudaStreamWaitEvent(w.stream, B->fork, 0));
     }
     for (Worker& w : B->workers)
         if (w.ctx->ws.cap < need) {
@@ -890,7 +917,17 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
                 if (gg.key == key) g = &gg;
             PointPlan& pl = plans[i];
             hotrg_status s;
-            if (!g) {
+            if (profiling) {
+                if ((s = plan_point(wc, p, imp_kind, pl, need)) != HOTRG_OK) {
+                    err = set_err(ctx, s, wc->last_error);
+                    break;
+                }
+                cudaMemcpyAsync(pl.dparams, &hp[i], sizeof(hotrg_params), cudaMemcpyHostToDevice, wk.stream);
+                if ((s = enqueue_point(wc, p, imp_kind, pl)) != HOTRG_OK) {
+                    err = set_err(ctx, s, wc->last_error);
+                    break;
+                }
+            } else if (!g) {
                 // first point of this class on this worker: run it directly, then capture the class's graph
                 if ((s = plan_point(wc, p, imp_kind, pl, need)) != HOTRG_OK) {
                     err = set_err(ctx, s, wc->last_error);
@@ -944,8 +981,19 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
                             cudaMemcpyDeviceToHost, wk.stream);
         }
     }
+    // join: the context stream waits for every worker (CUDA events recorded on it bracket the batch)
+    for (Worker& w : B->workers) {
+        cudaEventRecord(w.done, w.stream);
+        cudaStreamWaitEvent(ctx->stream, w.done, 0);
+    }
     for (Worker& w : B->workers) cudaStreamSynchronize(w.stream);
     if (cudaGetLastError() != cudaSuccess && err == HOTRG_OK) err = set_err(ctx, HOTRG_ECUDA, "batch execution failed");
+    if (profiling)
+        for (Worker& w : B->workers) {
+            prof_fold(w.ctx);
+            profile_add(ctx->prof.tot, w.ctx->prof.tot);
+            memset(&w.ctx->prof.tot, 0, sizeof(w.ctx->prof.tot));
+        }
     if (err == HOTRG_OK) {
         hotrg_status us = umma_check_status(ctx);
         if (us != HOTRG_OK) err = us;

@@ -58,3 +58,15 @@ def test_batch_with_invalid_entries(H, C):
     got = H.hotrg_run_batch(C.handle, pts, nstreams=2, check=False)
     assert got[1].status == H.EINVAL
     assert all(got[i].status == 0 for i in (0, 2, 3))
+
+
+def test_batch_with_profiling_equals_graph_replay(H, C):
+    pts = points(H, H.SPLIT_BF16)[:4]
+    replay = [r.lnz_per_site for r in C.run_batch(pts, nstreams=2)]
+    H.hotrg_profile_enable(C.handle, True)
+    got = [r.lnz_per_site for r in C.run_batch(pts, nstreams=2)]
+    prof = H.hotrg_profile_read(C.handle)
+    H.hotrg_profile_enable(C.handle, False)
+    assert got == replay
+    assert prof.steps == sum(p.n_steps for p in pts)
+    assert prof.gemm_calls[1] > 0 and prof.gemm_ms[1] > 0 and prof.eig_ms > 0
