@@ -50,6 +50,8 @@ def parse():
                     help="worker streams of the batch runner (1: points one after another on one stream)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
+    ap.add_argument("--block-sparse", type=int, default=1, choices=[0, 1],
+                    help="1: coarse contraction per U(1) charge block (the default form); 0: dense")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-form, accuracy and CPU legs")
     return ap.parse_args()
 
@@ -233,7 +235,8 @@ def main():
 
     def batch(step):
         base = (step * world + rank) * P
-        return [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec) for p in pts[base:base + P]]
+        return [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec, block_sparse=args.block_sparse)
+                for p in pts[base:base + P]]
 
     def run(plist):
         if args.nstreams > 1:
@@ -292,7 +295,11 @@ def main():
             "kernel_share_of_steps": coarse_ms / prof.step_ms if prof.step_ms else None,
             "traffic": KNOWN_TRAFFIC.get(source_hash())}
     breakdown = {"coarse_gemm_ms": coarse_ms, "env_gemm_ms": prof.gemm_ms[0], "slice_ms": prof.slice_ms,
-                 "eig_ms": prof.eig_ms, "steps_ms": prof.step_ms, "hotrg_steps": prof.steps,
+                 "eig_ms": prof.eig_ms, "eig_parts_ms": {"jacobi_small": prof.eig_part_ms[0],
+                                                          "subspace_fp32": prof.eig_part_ms[1],
+                                                          "rayleigh_ritz": prof.eig_part_ms[2],
+                                                          "select_projector": prof.eig_part_ms[3]},
+                 "steps_ms": prof.step_ms, "hotrg_steps": prof.steps,
                  "note": "CUDA-event time per region class summed over worker streams (regions overlap in time)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,

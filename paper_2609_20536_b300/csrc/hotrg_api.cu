@@ -65,8 +65,25 @@ void prof_end(hotrg_ctx* ctx, int handle, int cls, double flops) {
     m.flops = flops;
 }
 
+// Device-side flop counter of the block planner (its group sizes live on the device).
+hotrg_status prof_ensure_dflops(hotrg_ctx* ctx) {
+    if (ctx->prof.dflops) return HOTRG_OK;
+    HOTRG_CUDA_TRY(ctx, cudaMalloc(&ctx->prof.dflops, 64));
+    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->prof.dflops, 0, 64, ctx->stream));
+    return HOTRG_OK;
+}
+
 hotrg_status prof_fold(hotrg_ctx* ctx) {
     Profiler& P = ctx->prof;
+    if (P.on && P.dflops) {  // called after a stream synchronisation: the counter is final
+        double h[3] = {0.0, 0.0, 0.0};
+        if (cudaMemcpy(h, P.dflops, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            for (int c = 0; c < 3; ++c) P.tot.gemm_flops[c] += h[c];
+            cudaMemsetAsync(P.dflops, 0, sizeof(h), ctx->stream);
+            cudaStreamSynchronize(ctx->stream);
+        }
+        cudaGetLastError();
+    }
     for (ProfMark& m : P.pending) {
         float ms = 0.f;
         if (m.cls >= 0 && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
@@ -149,6 +166,10 @@ static hotrg_status check_params(hotrg_ctx* ctx, const hotrg_params* p) {
     if (p->env_policy < 0 || p->env_policy > 1) return set_err(ctx, HOTRG_EINVAL, "env_policy must be 0 or 1");
     if (p->prec != HOTRG_FP64 && !ctx->tc_ok)
         return set_err(ctx, HOTRG_ENOTSUP, "tensor-core forms need an sm_103 device");
+    if (p->block_sparse < 0 || p->block_sparse > 1 || p->reserved != 0)
+        return set_err(ctx, HOTRG_EINVAL, "block_sparse must be 0 or 1 and reserved 0");
+    if (p->block_sparse && p->prec == HOTRG_FP64)
+        return set_err(ctx, HOTRG_EINVAL, "block_sparse needs a split precision form");
     return HOTRG_OK;
 }
 
@@ -176,6 +197,14 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
                                   {(int64_t)Dp * Dv * Dv, (int64_t)Dp, (int64_t)n}};
     size_t g = 0;
     for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
+    if (p->block_sparse && p->prec != HOTRG_FP64) {
+        // grouped coarse products: (M, K, N) of s1, s2, s3
+        const int64_t gs[3][3] = {{(int64_t)Dp * Dh, Dh, (int64_t)Dh * Dv * Dv},
+                                  {(int64_t)Dp * Dh * Dv, (int64_t)hv, (int64_t)hv},
+                                  {(int64_t)Dp * Dv * Dv, (int64_t)n, (int64_t)Dp}};
+        for (auto& sh : gs)
+            g = std::max(g, bs_plan_bytes(sh[0], sh[1], sh[2]) + umma_grouped_workspace(sh[0], sh[1], sh[2]) + 4096);
+    }
     b += g;
     return b;
 }
@@ -304,6 +333,57 @@ static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, in
 }
 
 // One step; lnz_acc (device, may be null) += weight * ln c_k.
+// Block-sparse coarse contraction (split forms, pure runs with U(1) or Z2
+// labels).  Same s1 -> s2 -> s3 as coarse(), each contraction split into the
+// charge blocks of its index sets (q: labels of the legs, qh horizontal, qv
+// vertical, qn the new bond from the truncation):
+//   s1  M = (x, l2): q_x - q_l2     K = l1: q_l1           N = (r1, u, i): q_r1 - q_u + q_i
+//   s2  M = (x, r1, u): q_x - q_r1 + q_u   K = (l2, i): q_l2 + q_i   N = (d, r2): q_d + q_r2
+//   s3  M = (x, u, d): q_x + q_u - q_d     K = (r1, r2): q_r1 + q_r2  N = x': q_x'
+// These are the charge rules of P (q_x = q_a + q_b) and T (q_l + q_u = q_r + q_d)
+// rewritten for each product, so every element a later product reads is
+// written by the earlier one.  Tc is zeroed first: s3 writes only its blocks.
+static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const double* P, const int32_t* qh,
+                                  const int32_t* qv, const int32_t* qn, int Dh, int Dv, int Dp, const double* T_up,
+                                  const double* T_dn, double* W, double* Z, double* Tc, double* T_out) {
+    const int64_t h = Dh, v = Dv, p = Dp, hh = h * h, vv = v * v;
+    hotrg_status s;
+    auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const double* A, const double* B, double* C) {
+        const size_t mark = ctx->ws.used;
+        BsPlan pl;
+        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl);
+        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, A, B, C, PROF_GEMM_COARSE);
+        ctx->ws.used = mark;
+        return st;
+    };
+    // s1: W[x][l2][r1][u][i] = sum_l1 P[l1][l2][x] T_up[l1][r1][u][i]
+    {
+        BsSet M{2, {{qn, p, +1, 1, hh * vv}, {qh, h, -1, p, h * vv}}, p * h};
+        BsSet K{1, {{qh, h, +1, h * p, h * vv}}, h};
+        BsSet N{3, {{qh, h, +1, vv, vv}, {qv, v, -1, v, v}, {qv, v, +1, 1, 1}}, h * vv};
+        if ((s = run(M, K, N, P, T_up, W)) != HOTRG_OK) return s;
+    }
+    // s2: Z[x][r1][u][d][r2] = sum_{l2,i} W[x][l2][r1][u][i] T_dn[l2][r2][i][d]
+    {
+        BsSet M{3, {{qn, p, +1, hh * vv, h * vv * h}, {qh, h, -1, vv, vv * h}, {qv, v, +1, v, v * h}}, p * h * v};
+        BsSet K{2, {{qh, h, +1, h * vv, h * vv}, {qv, v, +1, 1, v}}, h * v};
+        BsSet N{2, {{qv, v, +1, 1, h}, {qh, h, +1, vv, 1}}, v * h};
+        if ((s = run(M, K, N, W, T_dn, Z)) != HOTRG_OK) return s;
+    }
+    // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][r1][u][d][r2] P[r1][r2][x']
+    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(Tc, 0, (size_t)p * vv * p * 8, ctx->stream));
+    {
+        BsSet M{3, {{qn, p, +1, h * vv * h, vv * p}, {qv, v, +1, v * h, v * p}, {qv, v, -1, h, p}}, p * vv};
+        BsSet K{2, {{qh, h, +1, vv * h, h * p}, {qh, h, +1, 1, p}}, hh};
+        BsSet N{1, {{qn, p, +1, 1, 1}}, p};
+        if ((s = run(M, K, N, Z, P, Tc)) != HOTRG_OK) return s;
+    }
+    // relabel for the other axis: T_out[u][d][x][x'] = Tc[x][u][d][x']
+    Perm po{4, {Dv, Dv, Dp, Dp}, {(int64_t)Dv * Dp, Dp, vv * Dp, 1}};
+    permute(ctx, Tc, T_out, po);
+    return HOTRG_OK;
+}
+
 static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double* T_in, const int32_t* q_h,
                             const int32_t* q_v, int Dh, int Dv, double* T_out, int32_t* q_out, int* dprime,
                             hotrg_step_info* info, const double* Ti_in, double* Ti_out, double* lnz_acc,
@@ -362,8 +442,14 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
         HOTRG_OK)
         return s;
     prof_end(ctx, h_eig, PROF_EIG, 0.0);
-    if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, T_out)) != HOTRG_OK)
+    const int sym = sym_of(p);
+    if (p->block_sparse && prec != HOTRG_FP64 && !Ti_in && sym != SYM_NONE) {
+        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, Tc, T_out)) !=
+            HOTRG_OK)
+            return s;
+    } else if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, T_out)) != HOTRG_OK) {
         return s;
+    }
     launch_norm(T_out, tn, partial, norm, ctx->stream);
     if (Ti_in) {
         // T_imp' = [P^T (T_imp above T) P + P^T (T above T_imp) P] / (2 c_k)
@@ -574,7 +660,7 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
 // Batched points: LPT over worker streams, one CUDA graph per point class.
 // ---------------------------------------------------------------------------
 struct ClassKey {
-    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z;
+    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z, block_sparse;
     double tie_rtol, eig_tol;
     bool operator==(const ClassKey& o) const { return memcmp(this, &o, sizeof(ClassKey)) == 0; }
 };
@@ -593,6 +679,7 @@ static ClassKey class_of(const hotrg_params* p, int imp_kind) {
     k.imp_kind = imp_kind;
     k.hz = p->h == 0.0;
     k.h1z = p->h1 == 0.0;
+    k.block_sparse = p->block_sparse;
     k.tie_rtol = p->tie_rtol;
     k.eig_tol = p->eig_tol;
     return k;
@@ -649,6 +736,7 @@ static void batch_free(Batch* b) {
             cudaStreamSynchronize(w.stream);
             if (w.ctx->ws.base) cudaFree(w.ctx->ws.base);
             for (cudaEvent_t e : w.ctx->prof.pool) cudaEventDestroy(e);
+            if (w.ctx->prof.dflops) cudaFree(w.ctx->prof.dflops);
             delete w.ctx;
         }
         if (w.done) cudaEventDestroy(w.done);
@@ -704,6 +792,7 @@ void hotrg_destroy(hotrg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     prof_fold(ctx);
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    if (ctx->prof.dflops) cudaFree(ctx->prof.dflops);
     if (ctx->ws.base) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->ws.base);
@@ -720,6 +809,12 @@ hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int32_t enable) {
     HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     prof_fold(ctx);
     ctx->prof.on = enable != 0;
+    if (ctx->prof.on) {
+        hotrg_status s = prof_ensure_dflops(ctx);
+        if (s != HOTRG_OK) return s;
+        HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->prof.dflops, 0, 64, ctx->stream));
+        HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
     memset(&ctx->prof.tot, 0, sizeof(ctx->prof.tot));
     ctx->prof.launch_base = g_launches.load();
     return HOTRG_OK;
@@ -866,6 +961,10 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
     HOTRG_CUDA_TRY(ctx, cudaEventRecord(B->fork, ctx->stream));
     for (Worker& w : B->workers) {
         w.ctx->prof.on = profiling;
+        if (profiling) {
+            hotrg_status s = prof_ensure_dflops(w.ctx);
+            if (s != HOTRG_OK) return set_err(ctx, s, w.ctx->last_error);
+        }
         HOTRG_CUDA_TRY(ctx, cudaStreamWaitEvent(w.stream, B->fork, 0));
     }
     for (Worker& w : B->workers)

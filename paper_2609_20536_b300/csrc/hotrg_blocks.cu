@@ -1,0 +1,225 @@
+// Charge-block planning for the block-sparse contractions.
+//
+// With U(1) (or Z2) symmetry the tensor obeys a charge rule: T[l,r,u,d] is
+// zero unless q_l + q_u = q_r + q_d (mod 2 for Z2), and the projector
+// P[a,b,x] is zero unless q_x = q_a + q_b (the fused charge of its sector,
+// §2.3.1).  Every contraction of a step, written as C = A B^T with row index
+// set M, contraction set K and column index set N, is then block diagonal:
+// each element of M, K and N carries a value v (a signed sum of its legs'
+// labels) and A[m, k] B[n, k] can be nonzero only when v(m) = v(k) = v(n).
+// The planner sorts each index set by v (a deterministic counting sort: one
+// warp per 1024-element chunk, ranks from warp vote masks, no atomics on the
+// order), and lays out one group per value present in both M and N:
+//   rows of the group  -> positions mbase .. mbase + M_g - 1 of the sorted M list
+//   padded slice rows  -> mpad .. mpad + round_up(M_g, 128) - 1
+//   tiles              -> tile_base .. + ceil(M_g/128) ceil(N_g/128) - 1.
+// For every position it stores the two element offsets the engine needs
+// (operand and output for M and N, A and B for K).  Groups whose value has
+// no element of K still get tiles: their block of C is zero and is written.
+#include "internal.cuh"
+
+namespace hotrg {
+
+__device__ __forceinline__ int bs_value(const BsSet& S, int sym, int64_t idx, int64_t& o0, int64_t& o1) {
+    int v = 0;
+    o0 = 0;
+    o1 = 0;
+    for (int f = S.nf - 1; f >= 0; --f) {
+        const int64_t i = idx % S.f[f].ext;
+        idx /= S.f[f].ext;
+        v += S.f[f].sgn * S.f[f].lab[i];
+        o0 += i * S.f[f].st0;
+        o1 += i * S.f[f].st1;
+    }
+    if (sym == SYM_Z2) v &= 1;
+    if (sym == SYM_NONE) v = 0;
+    return v;
+}
+
+constexpr int BS_WARPS = 8;  // warps per block in the counting passes
+
+// counts[chunk][BS_V]: elements of each value in every 1024-element chunk.
+__global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sym, int32_t* __restrict__ counts,
+                                                                 int64_t nchunks, int32_t* status) {
+    __shared__ int32_t tab[BS_WARPS][BS_V];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
+    for (int v = lane; v < BS_V; v += 32) tab[w][v] = 0;
+    __syncwarp();
+    if (chunk >= nchunks) return;
+    const int64_t lo = chunk * BS_CHUNK, hi = min(lo + BS_CHUNK, S.size);
+    for (int64_t b = lo; b < hi; b += 32) {
+        const int64_t idx = b + lane;
+        const bool act = idx < hi;
+        int64_t o0, o1;
+        const int v = act ? bs_value(S, sym, idx, o0, o1) + BS_VOFF : -1;
+        // an element whose value falls outside the table is left out here and in the
+        // placing pass alike (so every counted position is written) and fails the run
+        const bool ok = act && v >= 0 && v < BS_V;
+        if (act && !ok) atomicExch(status, (int)HOTRG_ENOTSUP);
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        const unsigned m = __match_any_sync(0xffffffffu, ok ? v : -1) & okm;
+        if (ok && (__ffs(m) - 1) == lane) tab[w][v] += __popc(m);
+        __syncwarp();
+    }
+    for (int v = lane; v < BS_V; v += 32) counts[chunk * BS_V + v] = tab[w][v];
+}
+
+// One block of BS_V threads: per-value totals and bases, per-chunk starts, the group table.
+__global__ void __launch_bounds__(BS_V) bs_scan_kernel(const int32_t* __restrict__ cM, int64_t nM,
+                                                       const int32_t* __restrict__ cK, int64_t nK,
+                                                       const int32_t* __restrict__ cN, int64_t nN,
+                                                       int32_t* __restrict__ sM, int32_t* __restrict__ sK,
+                                                       int32_t* __restrict__ sN, BsGroup* __restrict__ groups,
+                                                       BsHeader* __restrict__ hdr, double* flops_acc) {
+    __shared__ int64_t tot[3][BS_V], base[3][BS_V];
+    const int v = threadIdx.x;
+    const int32_t* cs[3] = {cM, cK, cN};
+    int32_t* ss[3] = {sM, sK, sN};
+    const int64_t ns[3] = {nM, nK, nN};
+    for (int s = 0; s < 3; ++s) {
+        int64_t t = 0;
+        for (int64_t c = 0; c < ns[s]; ++c) t += cs[s][c * BS_V + v];
+        tot[s][v] = t;
+    }
+    __syncthreads();
+    if (v == 0)
+        for (int s = 0; s < 3; ++s) {
+            int64_t run = 0;
+            for (int u = 0; u < BS_V; ++u) {
+                base[s][u] = run;
+                run += tot[s][u];
+            }
+        }
+    __syncthreads();
+    for (int s = 0; s < 3; ++s) {
+        int64_t run = base[s][v];
+        for (int64_t c = 0; c < ns[s]; ++c) {
+            ss[s][c * BS_V + v] = (int32_t)run;
+            run += cs[s][c * BS_V + v];
+        }
+    }
+    if (v == 0) {
+        int G = 0;
+        int64_t mpad = 0, npad = 0, tiles = 0;
+        double fl = 0.0;
+        for (int u = 0; u < BS_V; ++u) {
+            if (tot[0][u] == 0 || tot[2][u] == 0) continue;
+            BsGroup g;
+            g.mbase = base[0][u];
+            g.kbase = base[1][u];
+            g.nbase = base[2][u];
+            g.M = (int32_t)tot[0][u];
+            g.K = (int32_t)tot[1][u];
+            g.N = (int32_t)tot[2][u];
+            g.Kp = (g.K + 31) / 32 * 32;
+            g.mpad = mpad;
+            g.npad = npad;
+            g.tiles_n = (g.N + 127) / 128;
+            g.tile_base = (int32_t)tiles;
+            mpad += (g.M + 127) / 128 * 128;
+            npad += (g.N + 127) / 128 * 128;
+            tiles += (int64_t)((g.M + 127) / 128) * g.tiles_n;
+            fl += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+            groups[G++] = g;
+        }
+        hdr->G = G;
+        hdr->total_tiles = (int32_t)tiles;
+        hdr->mpad_total = mpad;
+        hdr->npad_total = npad;
+        hdr->flops = fl;
+        if (flops_acc) *flops_acc += fl;
+    }
+}
+
+// Writes the two offsets of every element at its sorted position.
+__global__ void __launch_bounds__(32 * BS_WARPS) bs_place_kernel(BsSet S, int sym, const int32_t* __restrict__ starts,
+                                                                 int64_t nchunks, int64_t* __restrict__ off0,
+                                                                 int64_t* __restrict__ off1) {
+    __shared__ int32_t tab[BS_WARPS][BS_V];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
+    if (chunk >= nchunks) return;
+    for (int v = lane; v < BS_V; v += 32) tab[w][v] = starts[chunk * BS_V + v];
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t lo = chunk * BS_CHUNK, hi = min(lo + BS_CHUNK, S.size);
+    for (int64_t b = lo; b < hi; b += 32) {
+        const int64_t idx = b + lane;
+        const bool act = idx < hi;
+        int64_t o0 = 0, o1 = 0;
+        int v = act ? bs_value(S, sym, idx, o0, o1) + BS_VOFF : -1;
+        const bool ok = act && v >= 0 && v < BS_V;
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        const unsigned m = __match_any_sync(0xffffffffu, ok ? v : -1) & okm;
+        int32_t pos = 0;
+        if (ok) pos = tab[w][v] + __popc(m & lt);
+        __syncwarp();
+        if (ok && (__ffs(m) - 1) == lane) tab[w][v] += __popc(m);
+        __syncwarp();
+        if (ok) {
+            off0[pos] = o0;
+            off1[pos] = o1;
+        }
+    }
+}
+
+static int64_t a256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN) {
+    size_t b = 0;
+    for (int64_t n : {nM, nK, nN}) {
+        const int64_t ch = (n + BS_CHUNK - 1) / BS_CHUNK;
+        b += 2 * a256(ch * BS_V * 4) + 2 * a256(n * 8);
+    }
+    return b + a256(sizeof(BsGroup) * BS_V) + a256(sizeof(BsHeader));
+}
+
+hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
+                     BsPlan& out) {
+    const BsSet* sets[3] = {&M, &K, &N};
+    int32_t* counts[3];
+    int32_t* starts[3];
+    int64_t* offs[3][2];
+    int64_t nch[3];
+    for (int s = 0; s < 3; ++s) {
+        nch[s] = (sets[s]->size + BS_CHUNK - 1) / BS_CHUNK;
+        counts[s] = (int32_t*)ws_alloc(ctx, nch[s] * BS_V * 4);
+        starts[s] = (int32_t*)ws_alloc(ctx, nch[s] * BS_V * 4);
+        offs[s][0] = (int64_t*)ws_alloc(ctx, sets[s]->size * 8);
+        offs[s][1] = (int64_t*)ws_alloc(ctx, sets[s]->size * 8);
+        if (!counts[s] || !starts[s] || !offs[s][0] || !offs[s][1])
+            return set_err(ctx, HOTRG_ENOMEM, "block plan workspace exhausted");
+    }
+    out.groups = (BsGroup*)ws_alloc(ctx, sizeof(BsGroup) * BS_V);
+    out.hdr = (BsHeader*)ws_alloc(ctx, sizeof(BsHeader));
+    if (!out.groups || !out.hdr) return set_err(ctx, HOTRG_ENOMEM, "block plan workspace exhausted");
+    int32_t* st = umma_status_word(ctx);
+    if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
+    cudaStream_t s = ctx->stream;
+    for (int i = 0; i < 3; ++i) {
+        const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
+        bs_count_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, counts[i], nch[i], st);
+    }
+    double* facc = (ctx->prof.on && ctx->prof.dflops) ? ctx->prof.dflops + prof_class : nullptr;
+    bs_scan_kernel<<<1, BS_V, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
+                                      starts[2], out.groups, out.hdr, facc);
+    for (int i = 0; i < 3; ++i) {
+        const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
+        bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], offs[i][0], offs[i][1]);
+    }
+    HOTRG_COUNT(7);
+    HOTRG_LAUNCH_CHECK(ctx, "block planner");
+    out.offM0 = offs[0][0];
+    out.offM1 = offs[0][1];
+    out.offK0 = offs[1][0];
+    out.offK1 = offs[1][1];
+    out.offN0 = offs[2][0];
+    out.offN1 = offs[2][1];
+    out.nM = M.size;
+    out.nK = K.size;
+    out.nN = N.size;
+    return HOTRG_OK;
+}
+
+}  // namespace hotrg

@@ -476,13 +476,82 @@ __device__ void cgs2_warp_t(float* Yt, int m, int b, uint32_t salt, float dep_to
     }
 }
 
+// Sum of v over the block, returned to every thread (red: >= 33 floats of shared memory).
+__device__ __forceinline__ float block_sum_f32(float v, float* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = lane < nw ? red[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    const float r = red[32];
+    __syncthreads();
+    return r;
+}
+
+// cgs2_warp_t on the whole block: the j dot products of each projection are
+// spread over the warps, the update and the norms over all threads.  Same
+// algorithm (two classical Gram-Schmidt passes, dependent columns replaced by
+// hashed random columns, at most four attempts), fixed reduction order.
+__device__ void cgs2_block_t(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* rbuf, float* red) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < b; ++j) {
+        float* yj = Yt + (int64_t)j * m;
+        bool done = false;
+        for (int attempt = 0; attempt < 4 && !done; ++attempt) {
+            if (attempt > 0) {
+                for (int t = tid; t < m; t += blockDim.x)
+                    yj[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)j);
+                __syncthreads();
+            }
+            float p0 = 0.f;
+            for (int t = tid; t < m; t += blockDim.x) p0 = fmaf(yj[t], yj[t], p0);
+            const float n0 = block_sum_f32(p0, red);
+            for (int pass = 0; pass < 2 && j > 0; ++pass) {
+                for (int i = wid; i < j; i += nw) {
+                    const float* yi = Yt + (int64_t)i * m;
+                    float acc = 0.f;
+                    for (int t = lane; t < m; t += 32) acc = fmaf(yi[t], yj[t], acc);
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) rbuf[i] = acc;
+                }
+                __syncthreads();
+                for (int t = tid; t < m; t += blockDim.x) {
+                    float acc = yj[t];
+                    for (int i = 0; i < j; ++i) acc = fmaf(-rbuf[i], Yt[(int64_t)i * m + t], acc);
+                    yj[t] = acc;
+                }
+                __syncthreads();
+            }
+            float p1 = 0.f;
+            for (int t = tid; t < m; t += blockDim.x) p1 = fmaf(yj[t], yj[t], p1);
+            const float nrm = block_sum_f32(p1, red);
+            if (nrm > dep_tol * dep_tol * n0 && nrm > 1e-30f) {
+                const float inv = rsqrtf(nrm);
+                for (int t = tid; t < m; t += blockDim.x) yj[t] *= inv;
+                done = true;
+            }
+            __syncthreads();
+        }
+        if (!done) {
+            for (int t = tid; t < m; t += blockDim.x) yj[t] = 0.f;
+            __syncthreads();
+        }
+    }
+}
+
 // FP32 block subspace iteration on one block: Qt, Yt are b x m (transposed);
-// the product Yt = (E_q Q)^T runs on all warps, the orthonormalisation on warp 0.
+// the product Yt = (E_q Q)^T and the orthonormalisation run on all warps.
 __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double* EL, const double* ER, int n,
                                                                     int iters, EigWs w) {
     __shared__ float Es[32][65];
     __shared__ float Qs[BCAP_MAX][65];
     __shared__ float rbuf[BCAP_MAX];
+    __shared__ float red[40];
     const int side = blockIdx.y;
     const double* E = side == 0 ? EL : ER;
     const int nsec = *w.nsec;
@@ -505,8 +574,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
         for (int64_t idx = threadIdx.x; idx < (int64_t)b * m; idx += blockDim.x)
             Q[idx] = hash_unit((uint32_t)(idx % m), (uint32_t)(idx / m));
         __syncthreads();
-        if (threadIdx.x < 32) cgs2_warp_t(Q, m, b, 1u, 1e-3f, rbuf);
-        __syncthreads();
+        cgs2_block_t(Q, m, b, 1u, 1e-3f, rbuf, red);
         for (int it = 0; it < iters; ++it) {
             // Yt[j][i] = sum_k Ef[i][k] Qt[j][k], tiles of 32 rows x 64 k
             for (int r0 = 0; r0 < m; r0 += 32) {
@@ -546,8 +614,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
                 }
             }
             __syncthreads();
-            if (threadIdx.x < 32) cgs2_warp_t(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, rbuf);
-            __syncthreads();
+            cgs2_block_t(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, rbuf, red);
             float* t = Q;  // the orthonormal Y becomes the next Q
             Q = Y;
             Y = t;

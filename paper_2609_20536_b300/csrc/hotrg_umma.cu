@@ -833,6 +833,397 @@ hotrg_status umma_contract(hotrg_ctx* ctx, int prec, int M, int N, int K, const 
     return umma_gemm_fmt(ctx, prec, M, N, K, A, FMT_F64, lda, B, FMT_F64, ldb, C, FMT_F64, ldc, true);
 }
 
+// ---------------------------------------------------------------------------
+// Grouped (block-sparse) contraction: the groups of a BsPlan (one per charge
+// value) share one slice buffer per operand, laid out group after group with
+// every group padded to 128 rows; row pitch = the K set's size rounded up to
+// 32.  Operand element (m, k) of group g is X[rowoff[mbase_g + m] + koff[kbase_g + k]]
+// and output element (m, n) goes to C[rowC[mbase_g + m] + colC[nbase_g + n]].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int group_of_row(const BsGroup* gr, int G, int64_t r, bool b_side) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((b_side ? gr[mid].npad : gr[mid].mpad) <= r)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// One warp per padded slice row; rows beyond the plan's padded total leave at once.
+__global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
+    const double* __restrict__ X, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ koff,
+    const BsGroup* __restrict__ groups, const BsHeader* __restrict__ hdr, int b_side, int NS, int Kp,
+    __nv_bfloat16* __restrict__ out, int64_t slice_stride, int32_t* __restrict__ exps) {
+    extern __shared__ uint64_t srow_all[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * GATHER_WARPS + wib;
+    const int G = hdr->G;
+    if (G == 0 || r >= (b_side ? hdr->npad_total : hdr->mpad_total)) return;
+    const int g = group_of_row(groups, G, r, b_side != 0);
+    const BsGroup gr = groups[g];
+    const int64_t local = r - (b_side ? gr.npad : gr.mpad);
+    const int rows = b_side ? gr.N : gr.M;
+    const int K = gr.K, Kg = gr.Kp;
+    const int64_t* kof = koff + gr.kbase;
+    __nv_bfloat16* o0 = out + r * Kp;
+    if (local >= rows) {  // padding row of the group's last tile
+        if (lane == 0) exps[r] = 0;
+        for (int k = lane; k < Kg; k += 32)
+            for (int p = 0; p < NS; ++p) o0[p * slice_stride + k] = __float2bfloat16_rn(0.f);
+        return;
+    }
+    const int64_t rbase = rowoff[(b_side ? gr.nbase : gr.mbase) + local];
+    const bool cached = K <= GATHER_SMEM_K;
+    uint64_t* srow = srow_all + (size_t)wib * GATHER_SMEM_K;
+    int emax = -2000;
+    for (int k = lane; k < K; k += 32) {
+        const uint64_t bits = ((const uint64_t*)X)[rbase + kof[k]];
+        if (cached) srow[k] = bits;
+        emax = max(emax, exp_f64(__longlong_as_double((long long)bits)));
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    __syncwarp();
+    const int e = emax <= -2000 ? 0 : emax + 1;
+    if (lane == 0) exps[r] = e;
+    const int T = SLICE_B1 + 8 * (NS - 1);
+    for (int k = lane; k < Kg; k += 32) {
+        int64_t F = 0;
+        if (k < K && emax > -2000) {
+            const uint64_t bits = cached ? srow[k] : ((const uint64_t*)X)[rbase + kof[k]];
+            const double d = __longlong_as_double((long long)bits);
+            const int64_t a = (int64_t)fixed_f64(d, T - e);
+            F = d < 0.0 ? -a : a;
+        }
+        int64_t rem = F;
+        for (int p = 0; p < NS; ++p) {
+            const int sh = 8 * (NS - 1 - p);
+            int64_t c;
+            if (sh == 0) {
+                c = rem;
+            } else {
+                c = (rem + (1ll << (sh - 1))) >> sh;
+                rem -= c << sh;
+            }
+            o0[p * slice_stride + k] = __float2bfloat16_rn(ldexpf((float)c, -8 * p));
+        }
+    }
+}
+
+struct GroupArgs {
+    const BsGroup* groups;
+    const BsHeader* hdr;
+    const int32_t* eA;
+    const int32_t* eB;
+    const int64_t* rowC;
+    const int64_t* colC;
+    double* C;
+    int32_t* status;
+};
+
+// Bounded wait that also gives up when this CTA has already failed.
+__device__ __forceinline__ bool mbar_wait_cta(uint64_t* bar, uint32_t parity, const int32_t* status,
+                                              const int* s_fail) {
+    for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255u) == 255u &&
+            (*(volatile const int32_t*)status != 0 || *(volatile const int*)s_fail != 0))
+            return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void decode_tile(const BsGroup* gr, int G, int t, int& g, int& tm, int& tn) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gr[mid].tile_base <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    g = lo;
+    const int loc = t - gr[g].tile_base;
+    tm = loc / gr[g].tiles_n;
+    tn = loc % gr[g].tiles_n;
+}
+
+// Persistent grouped GEMM: CTA b takes tiles b, b + gridDim.x, ...  The stage,
+// k-block and chunk counters run on across tiles, so the epilogue of one
+// tile (after its TMEM drain) overlaps the MMAs of the next.
+template <int NS>
+__global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                   const __grid_constant__ CUtensorMap tmB,
+                                                                   GroupArgs args) {
+    using Cfg = UmmaCfg<NS>;
+    constexpr int STAGES = Cfg::STAGES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* chunk_full = empty + STAGES;
+    uint64_t* chunk_empty = chunk_full + 1;
+    uint32_t* tmem_slot = (uint32_t*)(chunk_empty + 1);
+    int* s_fail = (int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = args.hdr->G;
+    const int total = args.hdr->total_tiles;
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = *(volatile const int32_t*)args.status;
+    __syncthreads();
+    if (s_abort != 0 || G == 0 || (int)blockIdx.x >= total) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(chunk_full, 1);
+        mbar_init(chunk_empty, EPI_WARPS);
+        *s_fail = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int g, tm, tn;
+                decode_tile(args.groups, G, t, g, tm, tn);
+                const BsGroup gr = args.groups[g];
+                const int nkb = gr.Kp / BK;
+                const int arow = (int)(gr.mpad + (int64_t)tm * BM), brow = (int)(gr.npad + (int64_t)tn * BN);
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int s = it % STAGES;
+                    if (it >= (uint32_t)STAGES &&
+                        !mbar_wait_cta(&empty[s], ((it / STAGES) - 1) & 1, args.status, s_fail)) {
+                        *s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + s * Cfg::STAGE;
+                    uint8_t* sb = sa + NS * Cfg::A_SLICE;
+                    mbar_arrive_expect_tx(&full[s], Cfg::STAGE);
+                    tma_load_3d(sa, &tmA, &full[s], kb * BK, arow, 0);
+                    tma_load_3d(sb, &tmB, &full[s], kb * BK, brow, 0);
+                    ++it;
+                }
+            }
+            // every issued load must have landed before the CTA may exit
+            const uint32_t first = it > (uint32_t)STAGES ? it - STAGES : 0;
+            for (uint32_t k = first; k < it; ++k)
+                if (!mbar_wait(&full[k % STAGES], (k / STAGES) & 1, args.status)) *s_fail = 1;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            const uint32_t acc0 = tmem, acc1 = tmem + BN, acc2 = tmem + 2 * BN;
+            uint32_t it = 0, ch = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int g, tm, tn;
+                decode_tile(args.groups, G, t, g, tm, tn);
+                const int nkb = args.groups[g].Kp / BK;
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int s = it % STAGES;
+                    const bool chunk_start = (kb % KCB) == 0;
+                    if (chunk_start && ch > 0) {
+                        if (!mbar_wait_cta(chunk_empty, (ch - 1) & 1, args.status, s_fail)) {
+                            *s_fail = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    if (!mbar_wait_cta(&full[s], (it / STAGES) & 1, args.status, s_fail)) {
+                        *s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * Cfg::STAGE);
+                    const uint32_t sb = sa + NS * Cfg::A_SLICE;
+#pragma unroll
+                    for (int kk = 0; kk < BK / UK; ++kk) {
+                        const uint32_t koff = kk * UK * 2;
+                        const uint32_t keep = (chunk_start && kk == 0) ? 0u : 1u;
+                        umma_bf16(acc0, sdesc_sw64(sa + koff), sdesc_sw64(sb + koff), idesc, keep);
+                        umma_bf16(acc1, sdesc_sw64(sa + koff), sdesc_sw64(sb + Cfg::B_SLICE + koff), idesc, keep);
+                        umma_bf16(acc1, sdesc_sw64(sa + Cfg::A_SLICE + koff), sdesc_sw64(sb + koff), idesc, 1u);
+                        bool first2 = keep == 0u;
+#pragma unroll
+                        for (int p = 0; p < NS; ++p) {
+#pragma unroll
+                            for (int q = 0; q < NS; ++q) {
+                                if (p + q < 2 || p + q > NS - 1) continue;
+                                umma_bf16(acc2, sdesc_sw64(sa + p * Cfg::A_SLICE + koff),
+                                          sdesc_sw64(sb + q * Cfg::B_SLICE + koff), idesc, first2 ? 0u : 1u);
+                                first2 = false;
+                            }
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                    ++it;
+                    if ((kb % KCB) == KCB - 1 || kb == nkb - 1) {
+                        umma_commit(chunk_full);
+                        ++ch;
+                    }
+                }
+            }
+            if (!ok) umma_commit(chunk_full);  // release the epilogue; s_fail marks the result invalid
+        }
+    } else {
+        const int quad = warp & 3;
+        const int colbase = ((warp - 2) >> 2) * 64;
+        const int row_local = quad * 32 + lane;
+        uint32_t ch = 0;
+        bool alive = true;
+        for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
+            int g, tm, tn;
+            decode_tile(args.groups, G, t, g, tm, tn);
+            const BsGroup gr = args.groups[g];
+            const int nchunks = (gr.Kp / BK + KCB - 1) / KCB;
+            float hi[64], lo[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                hi[j] = 0.f;
+                lo[j] = 0.f;
+            }
+            for (int c = 0; c < nchunks; ++c, ++ch) {
+                alive = __all_sync(0xffffffffu,
+                                   (alive && mbar_wait_cta(chunk_full, ch & 1, args.status, s_fail)) ? 1 : 0) != 0;
+                if (!alive) {
+                    *s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    uint32_t r0[8], r1[8], r2[8];
+                    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + colbase + q * 8;
+                    tmem_ld8(taddr, r0);
+                    tmem_ld8(taddr + BN, r1);
+                    tmem_ld8(taddr + 2 * BN, r2);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        df_accumulate(hi[q * 8 + j], lo[q * 8 + j], __uint_as_float(r0[j]), __uint_as_float(r1[j]),
+                                      __uint_as_float(r2[j]));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(chunk_empty);
+            }
+            if (!alive) break;
+            const int lrow = tm * BM + row_local;
+            if (lrow < gr.M) {
+                const int64_t roff = args.rowC[gr.mbase + lrow];
+                const int ea = args.eA[gr.mpad + lrow];
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const int lcol = tn * BN + colbase + j;
+                    if (lcol < gr.N) {
+                        const int sc = ea + args.eB[gr.npad + lcol] - 2 * SLICE_B1;
+                        args.C[roff + args.colC[gr.nbase + lcol]] = ldexp((double)hi[j] + (double)lo[j], sc);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)Cfg::TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *s_fail) atomicExch(args.status, (int)HOTRG_ETIMEOUT);
+}
+
+size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN) {
+    const int64_t Kp = round_up(nK, BK);
+    const int64_t rA = round_up(nM, BM) + (int64_t)BS_V * BM, rB = round_up(nN, BN) + (int64_t)BS_V * BN;
+    return (size_t)(5 * (rA + rB) * Kp * 2 + (rA + rB) * 4 + 4096);
+}
+
+template <int NS>
+static hotrg_status launch_grouped(hotrg_ctx* ctx, const __nv_bfloat16* As, int64_t rA, const __nv_bfloat16* Bs,
+                                   int64_t rB, int Kp, const GroupArgs& a, int prof_class) {
+    using Cfg = UmmaCfg<NS>;
+    static bool attr = false;
+    if (!attr) {
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 Cfg::SMEM));
+        attr = true;
+    }
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, As, NS, rA, Kp, BM) || !make_map(&mB, Bs, NS, rB, Kp, BN))
+        return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
+    const int h = prof_begin(ctx);
+    umma_grouped_kernel<NS><<<ctx->sm_count, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
+    prof_end(ctx, h, prof_class, 0.0);  // algorithmic flops are counted on the device by the planner
+    HOTRG_COUNT(1);
+    HOTRG_LAUNCH_CHECK(ctx, "umma_grouped_kernel");
+    return HOTRG_OK;
+}
+
+hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const double* A, const double* B, double* C,
+                          int prof_class) {
+    if (!ctx->tc_ok) return set_err(ctx, HOTRG_ENOTSUP, "tensor-core engine needs sm_103");
+    const int NS = ns_for(prec, prof_class == PROF_GEMM_COARSE);
+    const int Kp = (int)round_up(pl.nK, BK);
+    const int64_t rA = round_up(pl.nM, BM) + (int64_t)BS_V * BM, rB = round_up(pl.nN, BN) + (int64_t)BS_V * BN;
+    __nv_bfloat16* As = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * rA * Kp * 2);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * rB * Kp * 2);
+    int32_t* eA = (int32_t*)ws_alloc(ctx, (size_t)rA * 4);
+    int32_t* eB = (int32_t*)ws_alloc(ctx, (size_t)rB * 4);
+    if (!As || !Bs || !eA || !eB) return set_err(ctx, HOTRG_ENOMEM, "umma workspace exhausted");
+    int32_t* st = umma_status_word(ctx);
+    if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
+    static bool attr = false;
+    if (!attr) {
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 GATHER_WARPS * GATHER_SMEM_K * 8));
+        attr = true;
+    }
+    cudaStream_t s = ctx->stream;
+    const int smem = GATHER_WARPS * GATHER_SMEM_K * 8;
+    const int h_slice = prof_begin(ctx);
+    slice_grouped_kernel<<<(unsigned)((rA + GATHER_WARPS - 1) / GATHER_WARPS), 32 * GATHER_WARPS, smem, s>>>(
+        A, pl.offM0, pl.offK0, pl.groups, pl.hdr, 0, NS, Kp, As, rA * Kp, eA);
+    slice_grouped_kernel<<<(unsigned)((rB + GATHER_WARPS - 1) / GATHER_WARPS), 32 * GATHER_WARPS, smem, s>>>(
+        B, pl.offN0, pl.offK1, pl.groups, pl.hdr, 1, NS, Kp, Bs, rB * Kp, eB);
+    HOTRG_COUNT(2);
+    prof_end(ctx, h_slice, PROF_SLICE, 0.0);
+    HOTRG_LAUNCH_CHECK(ctx, "slice_grouped_kernel");
+    GroupArgs a;
+    a.groups = pl.groups;
+    a.hdr = pl.hdr;
+    a.eA = eA;
+    a.eB = eB;
+    a.rowC = pl.offM1;
+    a.colC = pl.offN1;
+    a.C = C;
+    a.status = st;
+    if (NS == 5) return launch_grouped<5>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    if (NS == 4) return launch_grouped<4>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    return launch_grouped<3>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+}
+
 hotrg_status umma_check_status(hotrg_ctx* ctx) {
     if (!g_status) return HOTRG_OK;
     int32_t h = 0;

@@ -28,6 +28,7 @@ struct ProfMark {
 
 struct Profiler {
     bool on = false;
+    double* dflops = nullptr;  // device: algorithmic flops counted by the block planner, per GEMM class
     std::vector<cudaEvent_t> pool;
     std::vector<ProfMark> pending;
     hotrg_profile tot{};
@@ -150,5 +151,54 @@ hotrg_status umma_check_status(hotrg_ctx* ctx);
 // (r/(rd1 rd2)) rs0 + ((r/rd2) % rd1) rs1 + (r % rd2) rs2 + (k/kd) ks0 + (k % kd) ks1.
 hotrg_status umma_contract_gather(hotrg_ctx* ctx, int prec, int M, int N, int K, const double* A, const int64_t* am,
                                   const double* B, const int64_t* bm, double* C, int64_t ldc, bool coarse);
+int32_t* umma_status_word(hotrg_ctx* ctx);
+
+// ---- block-sparse contractions (hotrg_blocks.cu, hotrg_umma.cu) -----------
+constexpr int BS_V = 128;       // charge values tracked per index set
+constexpr int BS_VOFF = 64;     // value v is stored at v + BS_VOFF (|v| < 64)
+constexpr int BS_CHUNK = 1024;  // elements per warp in the counting passes
+
+// One leg of an index set: its label array, extent, sign in the set's value,
+// and its element strides in the two tensors that use the set.
+struct BsFactor {
+    const int32_t* lab;
+    int64_t ext;
+    int sgn;
+    int64_t st0, st1;
+};
+// An index set of up to three legs, factor 0 the most significant digit.
+struct BsSet {
+    int nf;
+    BsFactor f[3];
+    int64_t size;
+};
+struct BsGroup {  // one charge block of a grouped contraction
+    int64_t mbase, kbase, nbase;  // first positions in the sorted M / K / N lists
+    int64_t mpad, npad;           // first padded slice rows of the group's A / B rows
+    int32_t M, K, N, Kp;
+    int32_t tiles_n, tile_base;
+};
+struct BsHeader {
+    int32_t G, total_tiles;
+    int64_t mpad_total, npad_total;
+    double flops;  // sum over groups of 2 M K N
+};
+struct BsPlan {  // device pointers (workspace) plus the host-known set sizes
+    BsGroup* groups;
+    BsHeader* hdr;
+    int64_t *offM0, *offM1;  // M set: offsets in A, in C
+    int64_t *offK0, *offK1;  // K set: offsets in A, in B
+    int64_t *offN0, *offN1;  // N set: offsets in B, in C
+    int64_t nM, nK, nN;
+};
+size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
+// Enqueues the planner for C = A B^T over index sets (M, K, N) with the given
+// symmetry; a label sum outside |v| < 64 records HOTRG_ENOTSUP in the engine's
+// status word.
+hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
+                     BsPlan& out);
+size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN);
+hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const double* A, const double* B, double* C,
+                          int prof_class);
 
 }  // namespace hotrg

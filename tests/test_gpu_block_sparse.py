@@ -1,0 +1,97 @@
+"""Block-sparse coarse contraction (block_sparse = 1) against the oracle and
+against the dense split form.
+
+The charge blocks hold every nonzero product of the dense contraction, so the
+result equals the dense form's up to the split form's own error (the slices
+accumulate over different exact chunks once the zeros are dropped), and the
+oracle's within the split form's tolerance.
+"""
+import pytest
+
+from oracle import gxy
+from oracle import hotrg as OH
+
+from parity_points import BATCH, SPLIT_SHAPES
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2609_20536_b300 import build
+    build.build()
+    from paper_2609_20536_b300 import hotrg
+    return hotrg
+
+
+@pytest.fixture(scope="module")
+def C(H):
+    c = H.Context()
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("beta,delta,nm,dcut,steps", SPLIT_SHAPES)
+def test_block_sparse_lnz_against_oracle(H, C, beta, delta, nm, dcut, steps):
+    ref = OH.run_gxy(beta, delta, nm, dcut, steps)
+    bs = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+    dense = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16)])[0]
+    assert bs.status == 0
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-9, bs.lnz_per_site - ref.lnz_per_site
+    # both carry the split form's ~1e-11..1e-10 error, from different exact chunks (the blocks drop zeros)
+    assert abs(bs.lnz_per_site - dense.lnz_per_site) <= 2e-10
+    for k, rs in enumerate(ref.steps):
+        assert bs.step[k].dprime == rs.Dp
+        assert bs.step[k].side == dense.step[k].side
+        assert abs(bs.step[k].ln_c - rs.ln_c) <= 1e-7 * max(1.0, abs(rs.ln_c))
+
+
+def test_block_sparse_z2_field(H, C):
+    # h1 != 0 keeps only the parity of the charge: two blocks
+    ref = OH.run_gxy(1.1, 0.4, 3, 16, 14, h1=0.03)
+    bs = C.run([H.params(1.1, 0.4, 3, 16, 14, h1=0.03, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-9
+
+
+def test_block_sparse_ising(H, C):
+    ref = OH.hotrg_run(gxy.ising_tensor(0.6), gxy.ising_charges(), 30, 16, "z2")
+    bs = C.run([H.params(0.6, 0.0, 0, 16, 30, tkind=H.T_ISING, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-9
+
+
+def test_block_sparse_without_structure_is_the_dense_form(H, C):
+    # h != 0 leaves no conserved label, and an impurity run keeps the dense path: bitwise equal
+    a = C.run([H.params(1.1, 0.4, 2, 12, 10, h=0.02, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+    b = C.run([H.params(1.1, 0.4, 2, 12, 10, h=0.02, prec=H.SPLIT_BF16)])[0]
+    assert a.lnz_per_site == b.lnz_per_site
+    a = C.run([H.params(1.1, 0.4, 2, 12, 10, h1=0.02, prec=H.SPLIT_BF16, block_sparse=1)], imp_kind=H.T_IMP_M1)[0]
+    b = C.run([H.params(1.1, 0.4, 2, 12, 10, h1=0.02, prec=H.SPLIT_BF16)], imp_kind=H.T_IMP_M1)[0]
+    assert a.lnz_per_site == b.lnz_per_site and a.imp_ratio == b.imp_ratio
+
+
+def test_block_sparse_batch_replay_equals_single_runs(H, C):
+    pts = [H.params(*pt, prec=H.SPLIT_BF16, block_sparse=1) for pt in BATCH]
+    single = [C.run([p])[0].lnz_per_site for p in pts]
+    for _ in range(2):  # the second call replays the captured graphs
+        got = C.run_batch(pts, nstreams=3)
+        assert [r.lnz_per_site for r in got] == single
+
+
+def test_block_sparse_rejects_fp64_form(H, C):
+    with pytest.raises(H.HotrgError) as e:
+        C.run([H.params(1.0, 0.5, 2, 8, 4, prec=H.FP64, block_sparse=1)])
+    assert e.value.status == H.EINVAL
+
+
+def test_block_sparse_profile_counts_block_flops(H, C):
+    p = H.params(1.0, 0.5, 2, 16, 12, prec=H.SPLIT_BF16, block_sparse=1)
+    H.hotrg_profile_enable(C.handle, True)
+    C.run([p])
+    bs = H.hotrg_profile_read(C.handle)
+    H.hotrg_profile_enable(C.handle, True)
+    C.run([H.params(1.0, 0.5, 2, 16, 12, prec=H.SPLIT_BF16)])
+    dense = H.hotrg_profile_read(C.handle)
+    H.hotrg_profile_enable(C.handle, False)
+    # the blocks hold a small fraction of the dense products
+    assert 0 < bs.gemm_flops[1] < 0.5 * dense.gemm_flops[1]
+    assert bs.gemm_calls[1] == dense.gemm_calls[1]
