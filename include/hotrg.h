@@ -90,10 +90,11 @@ typedef struct {
     double side_rtol;    /* eps_2 wins only if eps_2 < eps_1 (1 - side_rtol) (default 1e-6 when <= 0):
                             mirror-image environments give eps_1 = eps_2, which must not be decided by
                             the rounding of the eigenvalue sums */
-    int32_t block_sparse; /* 1: the coarse contraction (s1, s2, s3) runs per charge block (the U(1) or
-                             Z2 structure of the block-sparse remark of §2.3.1); split forms only, and
-                             only pure runs: with an impurity tensor or h != 0 it has no effect.  The
-                             result equals the dense form's up to rounding. */
+    int32_t block_sparse; /* 1: the environments (A, B, E) and the coarse contraction (s1, s2, s3)
+                             run per charge block (the U(1) or Z2 structure of the block-sparse remark
+                             of §2.3.1); split forms only, and only pure runs: with an impurity tensor
+                             or h != 0 it has no effect.  The result equals the dense form's up to the
+                             split form's rounding. */
     int32_t reserved;    /* must be 0 */
 } hotrg_params;
 

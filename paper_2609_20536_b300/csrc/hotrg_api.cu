@@ -198,10 +198,12 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
     size_t g = 0;
     for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
     if (p->block_sparse && p->prec != HOTRG_FP64) {
-        // grouped coarse products: (M, K, N) of s1, s2, s3
-        const int64_t gs[3][3] = {{(int64_t)Dp * Dh, Dh, (int64_t)Dh * Dv * Dv},
+        // grouped products: (M, K, N) of s1, s2, s3 and of the environments' A, B and E
+        const int64_t gs[5][3] = {{(int64_t)Dp * Dh, Dh, (int64_t)Dh * Dv * Dv},
                                   {(int64_t)Dp * Dh * Dv, (int64_t)hv, (int64_t)hv},
-                                  {(int64_t)Dp * Dv * Dv, (int64_t)n, (int64_t)Dp}};
+                                  {(int64_t)Dp * Dv * Dv, (int64_t)n, (int64_t)Dp},
+                                  {(int64_t)hv, (int64_t)hv, (int64_t)hv},
+                                  {(int64_t)n, (int64_t)Dv * Dv, (int64_t)n}};
         for (auto& sh : gs)
             g = std::max(g, bs_plan_bytes(sh[0], sh[1], sh[2]) + umma_grouped_workspace(sh[0], sh[1], sh[2]) + 4096);
     }
@@ -265,6 +267,58 @@ static hotrg_status environment(hotrg_ctx* ctx, int prec, const double* T, int D
 }
 
 // T_out[u][d][x][x'] = sum P[l1,l2,x] T_up[l1,r1,u,i] T_dn[l2,r2,i,d] P[r1,r2,x']
+// Block-sparse environment (split forms, U(1) or Z2 labels).  The same three
+// products as environment(), read straight out of T and written straight into
+// A2[a][a'][i][j], B2[a][a'][i][j] and E[a1][a2][a1'][a2'] through offset
+// tables (no permutation).  a is the truncated horizontal leg, b the other
+// one; the charge rule q_l + q_u = q_r + q_d gives the block values
+//   left  (a = l):  A: (a,i) q_a - q_i | (b,u) q_b - q_u    B: (a,i) q_a + q_i | (b,d) q_b + q_d
+//   right (a = r):  A: (a,i) q_a + q_i | (b,u) q_b + q_u    B: (a,i) q_a - q_i | (b,d) q_b - q_d
+//   E: K = (i, j) with q_i - q_j; M = (a1, a1') and N = (a2, a2') with the
+//      signs that make A[a1 i a1' j] and B[a2 i a2' j] nonzero.
+// Only the sector-diagonal blocks of E are written; the eigensolver reads no
+// other element.
+static hotrg_status environment_blocks(hotrg_ctx* ctx, int prec, int sym, const double* T, const int32_t* qh,
+                                       const int32_t* qv, int Dh, int Dv, bool right, double* A2, double* B2,
+                                       double* E) {
+    const int64_t h = Dh, v = Dv, vv = v * v;
+    const int64_t sL = h * vv, sR = vv, sU = v, sD = 1;
+    const int64_t sa = right ? sR : sL, sb = right ? sL : sR;
+    const int ga = right ? +1 : -1;  // sign of the vertical leg of (a, i) in A's value
+    auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const double* X, const double* Y, double* C) {
+        const size_t mark = ctx->ws.used;
+        BsPlan pl;
+        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_ENV, pl);
+        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, X, Y, C, PROF_GEMM_ENV);
+        ctx->ws.used = mark;
+        return st;
+    };
+    hotrg_status s;
+    // A[(a,i),(a',j)] = sum_{b,u} T(a, b, u, i = d) T(a', b, u, j = d)
+    {
+        BsSet M{2, {{qh, h, +1, sa, vv * h}, {qv, v, ga, sD, v}}, h * v};
+        BsSet K{2, {{qh, h, +1, sb, sb}, {qv, v, ga, sU, sU}}, h * v};
+        BsSet N{2, {{qh, h, +1, sa, vv}, {qv, v, ga, sD, 1}}, h * v};
+        if ((s = run(M, K, N, T, T, A2)) != HOTRG_OK) return s;
+    }
+    // B[(a,i),(a',j)] = sum_{b,d} T(a, b, i = u, d) T(a', b, j = u, d)
+    {
+        BsSet M{2, {{qh, h, +1, sa, vv * h}, {qv, v, -ga, sU, v}}, h * v};
+        BsSet K{2, {{qh, h, +1, sb, sb}, {qv, v, -ga, sD, sD}}, h * v};
+        BsSet N{2, {{qh, h, +1, sa, vv}, {qv, v, -ga, sU, 1}}, h * v};
+        if ((s = run(M, K, N, T, T, B2)) != HOTRG_OK) return s;
+    }
+    // E[a1][a2][a1'][a2'] = sum_{i,j} A2[a1][a1'][i][j] B2[a2][a2'][i][j]
+    {
+        const int sm = right ? -1 : +1;  // left: q_a1 - q_a1', q_a2' - q_a2; right: the negatives
+        BsSet M{2, {{qh, h, sm, h * vv, h * h * h}, {qh, h, -sm, vv, h}}, h * h};
+        BsSet K{2, {{qv, v, +1, v, v}, {qv, v, -1, 1, 1}}, vv};
+        BsSet N{2, {{qh, h, -sm, h * vv, h * h}, {qh, h, sm, vv, 1}}, h * h};
+        if ((s = run(M, K, N, A2, B2, E)) != HOTRG_OK) return s;
+    }
+    return HOTRG_OK;
+}
+
 static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, int Dv, int Dp,
                            const double* T_up, const double* T_dn, double* Pt, double* Pt2, double* Tt,
                            double* Tb, double* W, double* W2, double* Tc, double* T_out) {
@@ -423,9 +477,21 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
         return set_err(ctx, HOTRG_ENOMEM, "step workspace exhausted");
     hotrg_status s;
     const int h_step = prof_begin(ctx);
-    if ((s = environment(ctx, prec, T_in, Dh, Dv, false, X1, X2, Am, Bm, A2, B2, Ep, EL)) != HOTRG_OK) return s;
-    if (p->env_policy == 0)
-        if ((s = environment(ctx, prec, T_in, Dh, Dv, true, X1, X2, Am, Bm, A2, B2, Ep, ER)) != HOTRG_OK) return s;
+    const int sym = sym_of(p);
+    const bool blocks = p->block_sparse && prec != HOTRG_FP64 && !Ti_in && sym != SYM_NONE;
+    if (blocks) {
+        if ((s = environment_blocks(ctx, prec, sym, T_in, q_h, q_v, Dh, Dv, false, A2, B2, EL)) != HOTRG_OK)
+            return s;
+        if (p->env_policy == 0)
+            if ((s = environment_blocks(ctx, prec, sym, T_in, q_h, q_v, Dh, Dv, true, A2, B2, ER)) != HOTRG_OK)
+                return s;
+    } else {
+        if ((s = environment(ctx, prec, T_in, Dh, Dv, false, X1, X2, Am, Bm, A2, B2, Ep, EL)) != HOTRG_OK)
+            return s;
+        if (p->env_policy == 0)
+            if ((s = environment(ctx, prec, T_in, Dh, Dv, true, X1, X2, Am, Bm, A2, B2, Ep, ER)) != HOTRG_OK)
+                return s;
+    }
     EigPlan plan;
     plan.n = (int)n;
     plan.Dh = Dh;
@@ -442,8 +508,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
         HOTRG_OK)
         return s;
     prof_end(ctx, h_eig, PROF_EIG, 0.0);
-    const int sym = sym_of(p);
-    if (p->block_sparse && prec != HOTRG_FP64 && !Ti_in && sym != SYM_NONE) {
+    if (blocks) {
         if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, Tc, T_out)) !=
             HOTRG_OK)
             return s;
