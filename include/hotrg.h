@@ -85,7 +85,9 @@ typedef struct {
     int32_t m_range;     /* Bessel-sum range m in [-m_range, m_range]; the thesis uses 50 */
     int32_t eig_max_sweeps; /* Jacobi sweep cap (default 40 when <= 0) */
     int32_t tkind;       /* hotrg_tkind of the pure tensor: HOTRG_T_PURE or HOTRG_T_ISING */
-    double tie_rtol;     /* cut-cluster width relative to lambda_max (default 1e-12 when <= 0) */
+    double tie_rtol;     /* cut-cluster width relative to lambda_max (default 1e-9 when <= 0): wide
+                            enough that exactly degenerate charge-conjugate pairs stay tied under the
+                            split forms' ~1e-10 relative error */
     double eig_tol;      /* Jacobi stop: off-diagonal Frobenius <= eig_tol * ||E_q||_F (1e-15 when <= 0) */
     double side_rtol;    /* eps_2 wins only if eps_2 < eps_1 (1 - side_rtol) (default 1e-6 when <= 0):
                             mirror-image environments give eps_1 = eps_2, which must not be decided by

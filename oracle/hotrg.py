@@ -22,8 +22,12 @@ contractions, eigh for each symmetric eigenproblem) as the only primitives:
    D' = min(D_cut, D_h^2).  Following the block-sparse remark of §2.3.1, each
    symmetry sector of E (fixed fused charge l1 + l2) is diagonalised on its
    own.  Reading of an unstated point: eigenvalues within tie_rtol * lambda_max
-   of the D'-th largest form the cut cluster, filled by |q| ascending, then q
-   descending, then lambda descending; eps_2 wins only if
+   (1e-9) of the D'-th largest form the cut cluster, filled by |q| ascending,
+   then q descending, then lambda descending.  Charge conjugation makes the
+   +q and -q blocks' eigenvalues exactly equal; 1e-9 keeps such pairs tied
+   when the contractions carry ~1e-10 relative error (the split-precision
+   form), so the kept member of a pair at the cut is fixed by the rule, not
+   by rounding; eps_2 wins only if
    eps_2 < eps_1 * (1 - 1e-6), so ties keep the left side.  Mirror-image
    environments give eps_1 = eps_2 exactly; the 1e-6 margin keeps that tie
    from being decided by the rounding of the eigenvalue sums (about 1e-12
@@ -54,7 +58,7 @@ import numpy as np
 
 from . import gxy
 
-TIE_RTOL = 1e-12
+TIE_RTOL = 1e-9
 SIDE_RTOL = 1e-6
 
 

@@ -397,6 +397,7 @@ static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, in
 // These are the charge rules of P (q_x = q_a + q_b) and T (q_l + q_u = q_r + q_d)
 // rewritten for each product, so every element a later product reads is
 // written by the earlier one.  Tc is zeroed first: s3 writes only its blocks.
+// Offsets: W and Z are laid out per the comment below; T, P, Tc as usual.
 static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const double* P, const int32_t* qh,
                                   const int32_t* qv, const int32_t* qn, int Dh, int Dv, int Dp, const double* T_up,
                                   const double* T_dn, double* W, double* Z, double* Tc, double* T_out) {
@@ -410,25 +411,29 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
         ctx->ws.used = mark;
         return st;
     };
-    // s1: W[x][l2][r1][u][i] = sum_l1 P[l1][l2][x] T_up[l1][r1][u][i]
+    // The intermediates are stored so that each row of the next product's A
+    // operand is one contiguous block: W[x][r1][u][l2][i] (s2 row (x,r1,u), its K
+    // (l2,i) inside h v elements) and Z[x][u][d][r1][r2] (s3 row (x,u,d), K (r1,r2)).
+    // s1: W[x][r1][u][l2][i] = sum_l1 P[l1][l2][x] T_up[l1][r1][u][i]
     {
-        BsSet M{2, {{qn, p, +1, 1, hh * vv}, {qh, h, -1, p, h * vv}}, p * h};
+        BsSet M{2, {{qn, p, +1, 1, hh * vv}, {qh, h, -1, p, v}}, p * h};
         BsSet K{1, {{qh, h, +1, h * p, h * vv}}, h};
-        BsSet N{3, {{qh, h, +1, vv, vv}, {qv, v, -1, v, v}, {qv, v, +1, 1, 1}}, h * vv};
+        BsSet N{3, {{qh, h, +1, vv, v * h * v}, {qv, v, -1, v, h * v}, {qv, v, +1, 1, 1}}, h * vv};
         if ((s = run(M, K, N, P, T_up, W)) != HOTRG_OK) return s;
     }
-    // s2: Z[x][r1][u][d][r2] = sum_{l2,i} W[x][l2][r1][u][i] T_dn[l2][r2][i][d]
+    // s2: Z[x][u][d][r1][r2] = sum_{l2,i} W[x][r1][u][l2][i] T_dn[l2][r2][i][d]
     {
-        BsSet M{3, {{qn, p, +1, hh * vv, h * vv * h}, {qh, h, -1, vv, vv * h}, {qv, v, +1, v, v * h}}, p * h * v};
-        BsSet K{2, {{qh, h, +1, h * vv, h * vv}, {qv, v, +1, 1, v}}, h * v};
-        BsSet N{2, {{qv, v, +1, 1, h}, {qh, h, +1, vv, 1}}, v * h};
+        BsSet M{3, {{qn, p, +1, hh * vv, vv * hh}, {qh, h, -1, v * h * v, h}, {qv, v, +1, h * v, v * hh}},
+                p * h * v};
+        BsSet K{2, {{qh, h, +1, v, h * vv}, {qv, v, +1, 1, v}}, h * v};
+        BsSet N{2, {{qv, v, +1, 1, hh}, {qh, h, +1, vv, 1}}, v * h};
         if ((s = run(M, K, N, W, T_dn, Z)) != HOTRG_OK) return s;
     }
-    // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][r1][u][d][r2] P[r1][r2][x']
+    // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][u][d][r1][r2] P[r1][r2][x']
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(Tc, 0, (size_t)p * vv * p * 8, ctx->stream));
     {
-        BsSet M{3, {{qn, p, +1, h * vv * h, vv * p}, {qv, v, +1, v * h, v * p}, {qv, v, -1, h, p}}, p * vv};
-        BsSet K{2, {{qh, h, +1, vv * h, h * p}, {qh, h, +1, 1, p}}, hh};
+        BsSet M{3, {{qn, p, +1, vv * hh, vv * p}, {qv, v, +1, v * hh, v * p}, {qv, v, -1, hh, p}}, p * vv};
+        BsSet K{2, {{qh, h, +1, h, h * p}, {qh, h, +1, 1, p}}, hh};
         BsSet N{1, {{qn, p, +1, 1, 1}}, p};
         if ((s = run(M, K, N, Z, P, Tc)) != HOTRG_OK) return s;
     }
@@ -499,7 +504,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     plan.sym = sym_of(p);
     plan.max_sweeps = p->eig_max_sweeps > 0 ? p->eig_max_sweeps : 40;
     plan.tol = p->eig_tol > 0 ? p->eig_tol : 1e-15;
-    plan.tie_rtol = p->tie_rtol > 0 ? p->tie_rtol : 1e-12;
+    plan.tie_rtol = p->tie_rtol > 0 ? p->tie_rtol : 1e-9;
     plan.side_rtol = p->side_rtol > 0 ? p->side_rtol : 1e-6;
     plan.env_policy = p->env_policy;
     plan.exact = prec == HOTRG_FP64;

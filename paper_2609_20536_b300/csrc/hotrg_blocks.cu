@@ -8,7 +8,7 @@
 // each element of M, K and N carries a value v (a signed sum of its legs'
 // labels) and A[m, k] B[n, k] can be nonzero only when v(m) = v(k) = v(n).
 // The planner sorts each index set by v (a deterministic counting sort: one
-// warp per 1024-element chunk, ranks from warp vote masks, no atomics on the
+// warp per 256-element chunk, ranks from warp vote masks, no atomics on the
 // order), and lays out one group per value present in both M and N:
 //   rows of the group  -> positions mbase .. mbase + M_g - 1 of the sorted M list
 //   padded slice rows  -> mpad .. mpad + round_up(M_g, 128) - 1
@@ -20,16 +20,21 @@
 
 namespace hotrg {
 
-__device__ __forceinline__ int bs_value(const BsSet& S, int sym, int64_t idx, int64_t& o0, int64_t& o1) {
+// Value and the two offsets of element idx (sets have < 2^31 elements and
+// extents < 2^16, so the mixed-radix decode runs in 32-bit arithmetic).
+__device__ __forceinline__ int bs_value(const BsSet& S, int sym, int64_t idx64, int64_t& o0, int64_t& o1) {
     int v = 0;
     o0 = 0;
     o1 = 0;
+    uint32_t idx = (uint32_t)idx64;
     for (int f = S.nf - 1; f >= 0; --f) {
-        const int64_t i = idx % S.f[f].ext;
-        idx /= S.f[f].ext;
+        const uint32_t e = (uint32_t)S.f[f].ext;
+        const uint32_t q = idx / e;
+        const uint32_t i = idx - q * e;
+        idx = q;
         v += S.f[f].sgn * S.f[f].lab[i];
-        o0 += i * S.f[f].st0;
-        o1 += i * S.f[f].st1;
+        o0 += (int64_t)i * S.f[f].st0;
+        o1 += (int64_t)i * S.f[f].st1;
     }
     if (sym == SYM_Z2) v &= 1;
     if (sym == SYM_NONE) v = 0;
@@ -38,7 +43,7 @@ __device__ __forceinline__ int bs_value(const BsSet& S, int sym, int64_t idx, in
 
 constexpr int BS_WARPS = 8;  // warps per block in the counting passes
 
-// counts[chunk][BS_V]: elements of each value in every 1024-element chunk.
+// counts[chunk][BS_V]: elements of each value in every BS_CHUNK-element chunk.
 __global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sym, int32_t* __restrict__ counts,
                                                                  int64_t nchunks, int32_t* status) {
     __shared__ int32_t tab[BS_WARPS][BS_V];

@@ -479,6 +479,14 @@ __device__ void cgs2_warp_t(float* Yt, int m, int b, uint32_t salt, float dep_to
     }
 }
 
+// Blocks handled by subspace_fast_kernel (b <= 32 listed vectors, Q and Y in shared memory).
+constexpr int SUBF_BMAX = 32;
+constexpr int SUBF_SMEM = 200 * 1024;  // Q and Y: 2 b m floats
+
+__device__ __forceinline__ bool subf_ok(int b, int m) {
+    return b <= SUBF_BMAX && (size_t)2 * b * m * sizeof(float) <= (size_t)SUBF_SMEM;
+}
+
 // Sum of v over the block, returned to every thread (red: >= 33 floats of shared memory).
 __device__ __forceinline__ float block_sum_f32(float v, float* red) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -562,7 +570,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
         const int start = w.sec_start[sct];
         const int m = w.sec_start[sct + 1] - start;
         const int b = w.sec_b[sct];
-        if (b == m) continue;
+        if (b == m || subf_ok(b, m)) continue;  // Jacobi / subspace_fast_kernel
         const int64_t aoff = w.sec_aoff[sct];
         float* Ef = (float*)(w.A[side] + aoff);
         float* Q = (float*)(w.S1[side] + aoff);
@@ -627,6 +635,175 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
             float* dst = (float*)(w.S1[side] + aoff);
             for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) dst[idx] = Q[idx];
         }
+        __syncthreads();
+    }
+}
+
+// Fast path of the FP32 subspace iteration for blocks with b <= 32 listed
+// vectors whose Q and Y (b x m each, transposed) fit in shared memory:
+//  * Y = (E_q Q)^T one warp per row of E_q, the b sums of a row in registers
+//    and reduced with shuffles;
+//  * block CGS2 in panels of 8 columns (bcgs2_block), with the same
+//    dependent-column replacement as cgs2_warp_t.
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block CGS2 in panels of BCGS_PW columns on Yt (b x m in shared memory, row j =
+// column j).  For each panel: its columns are projected against all previous
+// columns twice by the whole block (dot products spread over the warps, then
+// one fused update), after which one warp runs CGS2 inside the panel.  A
+// column that is numerically dependent (its norm after projection <= dep_tol x
+// its norm before any projection) is replaced by a hashed random column and
+// projected against every previous column again, at most three times; a
+// column that stays dependent is zeroed.  R (BCGS_PW x b floats) and n0
+// (BCGS_PW floats) are shared-memory scratch.
+constexpr int BCGS_PW = 8;
+
+// y_c -= <y_i, y_c> y_i for i = lo .. hi-1 (modified Gram-Schmidt), twice; one warp.
+__device__ void proj_warp(float* Yt, int m, int c, int lo, int hi) {
+    const int lane = threadIdx.x & 31;
+    float* yc = Yt + c * m;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = lo; i < hi; ++i) {
+            const float* yi = Yt + i * m;
+            float acc = 0.f;
+            for (int t = lane; t < m; t += 32) acc = fmaf(yi[t], yc[t], acc);
+            acc = warp_sum_f(acc);
+            for (int t = lane; t < m; t += 32) yc[t] = fmaf(-acc, yi[t], yc[t]);
+            __syncwarp();
+        }
+    }
+}
+
+__device__ void bcgs2_block(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* R, float* n0) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int p0 = 0; p0 < b; p0 += BCGS_PW) {
+        const int pw = min(BCGS_PW, b - p0);
+        // norms before any projection (the dependency test's reference)
+        for (int c = warp; c < pw; c += nw) {
+            const float* yc = Yt + (p0 + c) * m;
+            float a = 0.f;
+            for (int t = lane; t < m; t += 32) a = fmaf(yc[t], yc[t], a);
+            a = warp_sum_f(a);
+            if (lane == 0) n0[c] = a;
+        }
+        __syncthreads();
+        for (int pass = 0; pass < 2 && p0 > 0; ++pass) {
+            for (int task = warp; task < p0 * pw; task += nw) {
+                const int i = task / pw, c = task % pw;
+                const float* yi = Yt + i * m;
+                const float* yc = Yt + (p0 + c) * m;
+                float a = 0.f;
+                for (int t = lane; t < m; t += 32) a = fmaf(yi[t], yc[t], a);
+                a = warp_sum_f(a);
+                if (lane == 0) R[c * SUBF_BMAX + i] = a;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < pw * m; idx += blockDim.x) {
+                const int c = idx / m, t = idx - c * m;
+                float acc = Yt[(p0 + c) * m + t];
+                for (int i = 0; i < p0; ++i) acc = fmaf(-R[c * SUBF_BMAX + i], Yt[i * m + t], acc);
+                Yt[(p0 + c) * m + t] = acc;
+            }
+            __syncthreads();
+        }
+        if (warp == 0) {
+            for (int c = p0; c < p0 + pw; ++c) {
+                float* yc = Yt + c * m;
+                float ref = n0[c - p0];
+                bool done = false;
+                for (int attempt = 0; attempt < 4 && !done; ++attempt) {
+                    if (attempt > 0) {
+                        for (int t = lane; t < m; t += 32)
+                            yc[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)c);
+                        __syncwarp();
+                        float a = 0.f;
+                        for (int t = lane; t < m; t += 32) a = fmaf(yc[t], yc[t], a);
+                        ref = warp_sum_f(a);
+                        proj_warp(Yt, m, c, 0, p0);  // a fresh column needs the earlier panels too
+                    }
+                    proj_warp(Yt, m, c, p0, c);
+                    float a = 0.f;
+                    for (int t = lane; t < m; t += 32) a = fmaf(yc[t], yc[t], a);
+                    const float nrm = warp_sum_f(a);
+                    if (nrm > dep_tol * dep_tol * ref && nrm > 1e-30f) {
+                        const float inv = rsqrtf(nrm);
+                        for (int t = lane; t < m; t += 32) yc[t] *= inv;
+                        done = true;
+                    }
+                    __syncwarp();
+                }
+                if (!done) {
+                    for (int t = lane; t < m; t += 32) yc[t] = 0.f;
+                    __syncwarp();
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double* EL, const double* ER, int n,
+                                                                    int iters, EigWs w) {
+    extern __shared__ float sq[];
+    __shared__ float Rs[BCGS_PW * SUBF_BMAX];
+    __shared__ float n0s[BCGS_PW];
+    const int side = blockIdx.y;
+    const double* E = side == 0 ? EL : ER;
+    const int nsec = *w.nsec;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
+        const int start = w.sec_start[sct];
+        const int m = w.sec_start[sct + 1] - start;
+        const int b = w.sec_b[sct];
+        if (b == m || !subf_ok(b, m)) continue;
+        const int64_t aoff = w.sec_aoff[sct];
+        float* Ef = (float*)(w.A[side] + aoff);
+        double* E64 = w.S3[side] + aoff;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
+            const int i = (int)(idx / m), j = (int)(idx % m);
+            const double v = E[(int64_t)w.members[start + i] * n + w.members[start + j]];
+            E64[idx] = v;
+            Ef[idx] = (float)v;
+        }
+        float* Q = sq;
+        float* Y = sq + b * m;
+        for (int idx = threadIdx.x; idx < b * m; idx += blockDim.x)
+            Q[idx] = hash_unit((uint32_t)(idx % m), (uint32_t)(idx / m));
+        __syncthreads();
+        bcgs2_block(Q, m, b, 1u, 1e-3f, Rs, n0s);
+        for (int it = 0; it < iters; ++it) {
+            for (int i = warp; i < m; i += nwarps) {
+                const float* er = Ef + (int64_t)i * m;
+                float acc[SUBF_BMAX];
+#pragma unroll
+                for (int j = 0; j < SUBF_BMAX; ++j) acc[j] = 0.f;
+                for (int k = lane; k < m; k += 32) {
+                    const float e = er[k];
+#pragma unroll
+                    for (int j = 0; j < SUBF_BMAX; ++j)
+                        if (j < b) acc[j] = fmaf(e, Q[j * m + k], acc[j]);
+                }
+                float mine = 0.f;
+#pragma unroll
+                for (int j = 0; j < SUBF_BMAX; ++j)
+                    if (j < b) {
+                        const float v = warp_sum_f(acc[j]);
+                        if (lane == j) mine = v;
+                    }
+                if (lane < b) Y[lane * m + i] = mine;
+            }
+            __syncthreads();
+            bcgs2_block(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, Rs, n0s);
+            float* t = Q;  // the orthonormal Y becomes the next Q
+            Q = Y;
+            Y = t;
+        }
+        // the final basis (b x m, transposed) goes to S1, as from subspace_fp32_kernel
+        float* dst = (float*)(w.S1[side] + aoff);
+        for (int idx = threadIdx.x; idx < b * m; idx += blockDim.x) dst[idx] = Q[idx];
         __syncthreads();
     }
 }
@@ -816,6 +993,25 @@ __device__ void bitonic_sort_idx(int* a, int npow2, const SelCmp& cmp) {
     }
 }
 
+// Reorders kept[0, k) by block key ascending, keeping the selection order
+// within a key (a gauge choice: the kept basis is only defined up to an
+// orthogonal map, and the next step's labels come out sorted, so every
+// charge-constrained index range of the next contractions is contiguous).
+__device__ void sort_kept_by_key(int* kept, int k, const int* slotkey, int* tmp) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const int ki = slotkey[kept[i]];
+        int r = 0;
+        for (int j = 0; j < k; ++j) {
+            const int kj = slotkey[kept[j]];
+            r += (kj < ki) || (kj == ki && j < i);
+        }
+        tmp[r] = kept[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += blockDim.x) kept[i] = tmp[i];
+}
+
 __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int dprime, double tie_rtol, EigWs w) {
     extern __shared__ int si[];
     __shared__ double red[40];
@@ -840,6 +1036,7 @@ __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int dprime, double
     if (n <= dprime) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) kept[i] = si[i];
         if (threadIdx.x == 0) *w.eps[side] = unl;
+        sort_kept_by_key(kept, n, slotkey, slotkey + MAX_N);
         return;
     }
     const double lmax = lam[si[0]];
@@ -893,6 +1090,7 @@ __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int dprime, double
     }
     const double tot = block_reduce_sum(s, red);
     if (threadIdx.x == 0) *w.eps[side] = tot + unl;
+    sort_kept_by_key(kept, dprime, slotkey, si);
 }
 
 // ---------------------------------------------------------------------------
@@ -939,6 +1137,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
                                                  MAX_N * 4 * 3));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)RR_SMEM_BYTES));
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(subspace_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 SUBF_SMEM));
         g_attr_done = true;
     }
     EigWs w = carve(ws, n);
@@ -970,12 +1170,14 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
     // on every block); the wider Z2 / no-symmetry blocks keep 12
     const int sub_iters = iters_override ? iters_override : (plan.sym == SYM_U1 ? SUB_ITERS_U1 : SUB_ITERS);
     const bool exact = plan.exact || force_exact == 1;
-    int small_thr = exact ? n : (bcap > 48 ? bcap : 48);
+    // blocks of at most bcap states get every eigenpair from FP64 Jacobi (b = m);
+    // larger ones list bcap through the subspace path
+    int small_thr = exact ? n : bcap;
     if (!exact && thr_override) small_thr = thr_override;
     const int hp0 = prof_begin(ctx);
     sectors_kernel<<<1, SORT_THREADS, MAX_N * 8, st>>>(q_h, plan.Dh, plan.sym, small_thr, bcap, w);
     HOTRG_COUNT(3);  // sectors, jacobi, select
-    HOTRG_COUNT(exact ? 1 : 5);  // projector (+ subspace, rr_prep, rr_product, rr_finish)
+    HOTRG_COUNT(exact ? 1 : 6);  // projector (+ two subspace kernels, rr_prep, rr_product, rr_finish)
     HOTRG_LAUNCH_CHECK(ctx, "sectors_kernel");
     const int sides = plan.env_policy == 0 ? 2 : 1;
     const int grid = n < 2 * ctx->sm_count ? n : 2 * ctx->sm_count;
@@ -986,6 +1188,7 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
     if (!exact) {
         const int sgrid = n < ctx->sm_count ? n : ctx->sm_count;
         const int hp1 = prof_begin(ctx);
+        subspace_fast_kernel<<<dim3(sgrid, sides), SUB_THREADS, SUBF_SMEM, st>>>(EL, ER, n, sub_iters, w);
         subspace_fp32_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(EL, ER, n, sub_iters, w);
         prof_end(ctx, hp1, PROF_EIG_PART0 + 1, 0.0);
         HOTRG_LAUNCH_CHECK(ctx, "subspace_fp32_kernel");

@@ -38,31 +38,44 @@ __device__ double bessel_in(int n, double x) {
 
 // a_n(beta, Delta) = sum_{m=-M..M} I_{n-2m}(beta Delta) I_m(beta (1 - Delta))   (Eq. 3.4)
 // F(Q) for the pure tensor (Eq. 3.15) and the impurities (Eq. 3.20, 3.21).
-__global__ void coeff_kernel(const hotrg_params* __restrict__ dp, int n_max, int m_range, int kind, double* a,
-                             double* F) {
+// One block: first every I_k needed (k = 0 .. kmax for the four arguments
+// beta Delta, beta (1 - Delta), beta h, beta h1) is tabulated in shared memory,
+// one thread per value; then one thread per coefficient sums the table in the
+// order of the formulas above.  All arguments are >= 0 and I_{-k} = I_k.
+__global__ void coeff_kernel(const hotrg_params* __restrict__ dp, int n_max, int m_range, int kind, int kmax,
+                             double* a, double* F) {
+    extern __shared__ double tab[];  // [4][kmax + 1]
     const double beta = dp->beta, delta = dp->delta, h = dp->h, h1 = dp->h1;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double xs[4] = {beta * delta, beta * (1.0 - delta), beta * h, beta * h1};
+    const int w = kmax + 1;
+    for (int i = threadIdx.x; i < 4 * w; i += blockDim.x) tab[i] = bessel_in(i % w, xs[i / w]);
+    __syncthreads();
+    const double* I1 = tab;          // I_k(beta Delta)
+    const double* I2 = tab + w;      // I_k(beta (1 - Delta))
+    const double* Ih = tab + 2 * w;  // I_k(beta h)
+    const double* Ih1 = tab + 3 * w; // I_k(beta h1)
+    auto at = [](const double* t, int k) { return t[k < 0 ? -k : k]; };
     const int na = 2 * n_max + 1;
     const int nf = 8 * n_max + 1;
-    if (t < na) {
-        const int n = t - n_max;
-        const double x1 = beta * delta, x2 = beta * (1.0 - delta);
-        double s = 0.0;
-        for (int m = -m_range; m <= m_range; ++m) s += bessel_in(n - 2 * m, x1) * bessel_in(m, x2);
-        a[t] = s;
-    } else if (t < na + nf) {
-        const int Q = (t - na) - 4 * n_max;
-        const double bh = beta * h, bh1 = beta * h1;
-        double s = 0.0;
-        for (int j = -m_range; j <= m_range; ++j) {
-            if (kind == HOTRG_T_PURE)
-                s += bessel_in(Q + 2 * j, bh) * bessel_in(j, bh1);
-            else if (kind == HOTRG_T_IMP_M)
-                s += bessel_in(j, bh1) * 0.5 * (bessel_in(Q + 2 * j - 1, bh) + bessel_in(Q + 2 * j + 1, bh));
-            else
-                s += bessel_in(Q + 2 * j, bh) * 0.5 * (bessel_in(j + 1, bh1) + bessel_in(j - 1, bh1));
+    for (int t = threadIdx.x; t < na + nf; t += blockDim.x) {
+        if (t < na) {
+            const int n = t - n_max;
+            double s = 0.0;
+            for (int m = -m_range; m <= m_range; ++m) s += at(I1, n - 2 * m) * at(I2, m);
+            a[t] = s;
+        } else {
+            const int Q = (t - na) - 4 * n_max;
+            double s = 0.0;
+            for (int j = -m_range; j <= m_range; ++j) {
+                if (kind == HOTRG_T_PURE)
+                    s += at(Ih, Q + 2 * j) * at(Ih1, j);
+                else if (kind == HOTRG_T_IMP_M)
+                    s += at(Ih1, j) * 0.5 * (at(Ih, Q + 2 * j - 1) + at(Ih, Q + 2 * j + 1));
+                else
+                    s += at(Ih, Q + 2 * j) * 0.5 * (at(Ih1, j + 1) + at(Ih1, j - 1));
+            }
+            F[t - na] = s;
         }
-        F[t - na] = s;
     }
 }
 
@@ -115,7 +128,9 @@ void launch_init_tensor(const hotrg_params* p, const hotrg_params* dp, int kind,
     int sym = SYM_U1;
     if (p->h != 0.0) sym = SYM_NONE;
     else if (p->h1 != 0.0) sym = SYM_Z2;
-    coeff_kernel<<<(na + nf + 127) / 128, 128, 0, st>>>(dp, n_max, m_range, kind, a, F);
+    // largest |order|: n_max + 2 m_range for a_n, 4 n_max + 2 m_range + 1 for F (<= 657 doubles a row)
+    const int kmax = 4 * n_max + 2 * m_range + 2;
+    coeff_kernel<<<1, 256, 4 * (kmax + 1) * sizeof(double), st>>>(dp, n_max, m_range, kind, kmax, a, F);
     const int total = na * na * na * na;
     gxy_tensor_kernel<<<(total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024, 256, 0, st>>>(
         a, F, n_max, sym, T, labels);
@@ -272,10 +287,14 @@ void launch_norm(const double* x, int64_t n, double* partial, double* norm, cuda
     HOTRG_COUNT(2);
 }
 
+// x <- x / c as x (1 / c): one FP64 multiply per element instead of a division
+// (B300's FP64 division made this pass 10x slower than its memory traffic).
+// The divisor differs from c by at most an ulp; ln c_k is recorded from c and
+// the next norm absorbs the difference.
 __global__ void scale_inv_kernel(double* x, int64_t n, const double* c) {
-    const double cc = *c;
+    const double inv = 1.0 / *c;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = x[i] / cc;
+        x[i] *= inv;
 }
 
 void launch_scale_inv(double* x, int64_t n, const double* c, cudaStream_t st) {

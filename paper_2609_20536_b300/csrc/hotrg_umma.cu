@@ -950,6 +950,20 @@ __device__ __forceinline__ void decode_tile(const BsGroup* gr, int G, int t, int
     tn = loc % gr[g].tiles_n;
 }
 
+// Shared memory of the grouped kernel: the stages plus a 32 x 17 FP64 staging
+// tile per epilogue warp, through which the output is written row-contiguous.
+template <int NS>
+struct GroupCfg {
+    static constexpr int A_SLICE = BM * BK * 2;
+    static constexpr int B_SLICE = BN * BK * 2;
+    static constexpr int STAGE = NS * (A_SLICE + B_SLICE);
+    static constexpr int STG_LD = 17;
+    static constexpr int STG_BYTES = EPI_WARPS * 32 * STG_LD * 8;
+    static constexpr int STAGES = (200 * 1024 - STG_BYTES) / STAGE >= 4 ? 4 : (200 * 1024 - STG_BYTES) / STAGE;
+    static constexpr int SMEM = STAGES * STAGE + STG_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int TMEM_COLS = 512;
+};
+
 // Persistent grouped GEMM: CTA b takes tiles b, b + gridDim.x, ...  The stage,
 // k-block and chunk counters run on across tiles, so the epilogue of one
 // tile (after its TMEM drain) overlaps the MMAs of the next.
@@ -957,11 +971,12 @@ template <int NS>
 __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
                                                                    GroupArgs args) {
-    using Cfg = UmmaCfg<NS>;
+    using Cfg = GroupCfg<NS>;
     constexpr int STAGES = Cfg::STAGES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE);
+    double* staging = (double*)(smem + STAGES * Cfg::STAGE);
+    uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE + Cfg::STG_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* chunk_full = empty + STAGES;
     uint64_t* chunk_empty = chunk_full + 1;
@@ -1129,18 +1144,34 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                 if (lane == 0) mbar_arrive(chunk_empty);
             }
             if (!alive) break;
-            const int lrow = tm * BM + row_local;
-            if (lrow < gr.M) {
-                const int64_t roff = args.rowC[gr.mbase + lrow];
-                const int ea = args.eA[gr.mpad + lrow];
+            // output: each lane holds one row; 16 columns at a time go through the warp's
+            // staging tile so that every store covers two rows x 16 consecutive columns
+            const int my_lrow = tm * BM + row_local;
+            const int row_ok = my_lrow < gr.M ? 1 : 0;
+            const int64_t my_roff = row_ok ? args.rowC[gr.mbase + my_lrow] : 0;
+            const int my_ea = args.eA[gr.mpad + my_lrow];
+            double* stg = staging + (warp - 2) * (32 * Cfg::STG_LD);
+            const int cl = lane & 15;
 #pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    const int lcol = tn * BN + colbase + j;
-                    if (lcol < gr.N) {
-                        const int sc = ea + args.eB[gr.npad + lcol] - 2 * SLICE_B1;
-                        args.C[roff + args.colC[gr.nbase + lcol]] = ldexp((double)hi[j] + (double)lo[j], sc);
-                    }
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                    stg[lane * Cfg::STG_LD + jj] = (double)hi[c0 + jj] + (double)lo[c0 + jj];
+                __syncwarp();
+                const int lcol = tn * BN + colbase + c0 + cl;
+                const bool col_ok = lcol < gr.N;
+                const int64_t coff = col_ok ? args.colC[gr.nbase + lcol] : 0;
+                const int ceb = col_ok ? args.eB[gr.npad + lcol] : 0;
+#pragma unroll 4
+                for (int r = 0; r < 16; ++r) {
+                    const int row = 2 * r + (lane >> 4);
+                    const int64_t roff = __shfl_sync(0xffffffffu, my_roff, row);
+                    const int ea = __shfl_sync(0xffffffffu, my_ea, row);
+                    const int rok = __shfl_sync(0xffffffffu, row_ok, row);
+                    if (rok && col_ok)
+                        args.C[roff + coff] = ldexp(stg[row * Cfg::STG_LD + cl], ea + ceb - 2 * SLICE_B1);
                 }
+                __syncwarp();
             }
         }
     }
@@ -1163,7 +1194,7 @@ size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN) {
 template <int NS>
 static hotrg_status launch_grouped(hotrg_ctx* ctx, const __nv_bfloat16* As, int64_t rA, const __nv_bfloat16* Bs,
                                    int64_t rB, int Kp, const GroupArgs& a, int prof_class) {
-    using Cfg = UmmaCfg<NS>;
+    using Cfg = GroupCfg<NS>;
     static bool attr = false;
     if (!attr) {
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
