@@ -4,7 +4,8 @@
 Workload: distinct (beta, Delta) points of the q = 2 generalized XY model,
 beta ~ U[0.5, 2.0], Delta ~ U[0, 1] (seed 20536), n_max = 4 (D0 = 9),
 D_cut = 64, 25 coarse-graining steps per point (2^25 sites), run through the
-C-ABI library (hotrg_run) in the split-BF16 precision form.  One bench step =
+C-ABI library (hotrg_run_batch on worker streams) in the split-BF16
+precision form with block-sparse (per U(1) charge block) contractions.  One bench step =
 one pass of the whole hot path (initial tensor, 25 HOTRG steps, closing
 trace) over `--points` points per GPU.  Several GPUs run independent
 replicas on distinct points (no collective on the data path).
@@ -36,6 +37,7 @@ UNIT = "points/s"
 D_CUT, N_MAX, N_STEPS = 64, 4, 25
 WORKLOAD = ("gXY q=2 HOTRG points, beta~U[0.5,2.0], Delta~U[0,1] (seed 20536), n_max=4 (D0=9), "
             "D_cut=64, 25 one-axis steps per point (2^25 sites), split-BF16 tensor-core form")
+WORKLOAD_BS = ", contractions per U(1) charge block"
 # ncu DRAM traffic of the coarse-contraction kernel, keyed by the source hash it was captured on
 KNOWN_TRAFFIC = {}
 
@@ -287,10 +289,13 @@ def main():
     slices = 15 if prec == H.SPLIT_BF16 else (6 if prec == H.SPLIT_BF16_FAST else 1)
     # a split form is bounded by the BF16 tensor pipe: every slice product is 2MNK of BF16 work
     achieved = fp64_equiv * slices
-    roof = {"bound": "tensor", "kernel": "umma_gemm_kernel (coarse contraction s1/s2/s3)",
+    kname = ("umma_grouped_kernel<5> (block-sparse coarse contraction s1/s2/s3)" if args.block_sparse
+             else "umma_gemm_kernel<5> (coarse contraction s1/s2/s3)")
+    roof = {"bound": "tensor", "kernel": kname,
             "achieved": achieved, "peak": sustained, "unit": "TFLOP/s", "frac": achieved / sustained,
             "peak_source": f"bf16 sustained, {src}",
-            "achieved_is": f"{slices} BF16 slice products x 2MNK per contraction / CUDA-event time on its stream",
+            "achieved_is": (f"{slices} BF16 slice products x 2MNK per contraction (per charge block, summed over "
+                            "blocks, when block-sparse) / CUDA-event time on its stream"),
             "slice_products": slices, "fp64_equivalent_tflops": fp64_equiv,
             "kernel_share_of_steps": coarse_ms / prof.step_ms if prof.step_ms else None,
             "traffic": KNOWN_TRAFFIC.get(source_hash())}
@@ -305,7 +310,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec != H.FP64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points_per_step": P, "worker_streams": args.nstreams,
+            "config": {"workload": WORKLOAD + (WORKLOAD_BS if args.block_sparse else ""), "points_per_step": P, "worker_streams": args.nstreams,
                        "d_cut": D_CUT, "n_max": N_MAX,
                        "n_steps": N_STEPS, "prec": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "working set above L2: 8.6 GB D^5 intermediates per HOTRG step"},
@@ -315,14 +320,14 @@ def main():
                     "note": "host wall clock around the synchronous hotrg_run_batch / hotrg_run C-ABI call: "
                             "params in, results out"}}
     if not args.no_extras and world == 1:
-        line.update(extras(H, ctx, pts, prec))
+        line.update(extras(H, ctx, pts, prec, args.block_sparse))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def extras(H, ctx, pts, prec):
-    """FP64-form timing at the same D_cut, accuracy against the oracle, CPU oracle baseline."""
+def extras(H, ctx, pts, prec, bs):
+    """FP64-form and dense-form timing at the same D_cut, accuracy against the oracle, CPU oracle baseline."""
     out = {}
     import torch
     # FP64 form: first 3 steps of one point (step 3 is the first at full size)
@@ -334,16 +339,25 @@ def extras(H, ctx, pts, prec):
     r3 = ctx.run([H.params(p.beta, p.delta, p.n_max, p.d_cut, 3, prec=H.FP64)])[0]
     t3 = time.perf_counter() - t0 - t2
     fp64_point_s = t2 + (N_STEPS - 2) * t3
-    split3 = ctx.run([H.params(p.beta, p.delta, p.n_max, p.d_cut, 3, prec=prec)])[0]
+    split3 = ctx.run([H.params(p.beta, p.delta, p.n_max, p.d_cut, 3, prec=prec, block_sparse=bs)])[0]
     out["fp64_form"] = {"value": 1.0 / fp64_point_s, "unit": UNIT, "s_per_full_step": t3,
                         "note": "FP64 SIMT form at the same workload, 3 steps timed, steps 3-25 taken equal",
                         "dlnz_split_vs_fp64_after_3_steps": split3.lnz_per_site - r3.lnz_per_site}
+    if bs:
+        # the dense split form (every contraction over all elements) on one point, for comparison
+        q = pts[1]
+        t0 = time.perf_counter()
+        rd = ctx.run([H.params(q.beta, q.delta, q.n_max, q.d_cut, q.n_steps, prec=prec)])[0]
+        td = time.perf_counter() - t0
+        rb = ctx.run([H.params(q.beta, q.delta, q.n_max, q.d_cut, q.n_steps, prec=prec, block_sparse=1)])[0]
+        out["dense_form"] = {"value": 1.0 / td, "unit": UNIT, "note": "split-BF16 form with dense contractions, "
+                             "one point, host wall clock", "dlnz_block_vs_dense": rb.lnz_per_site - rd.lnz_per_site}
     # accuracy of the timed form against the FP64 oracle on smaller points of the same family
     from oracle import hotrg as OH
     errs = []
     for q in pts[:3]:
         ref = OH.run_gxy(q.beta, q.delta, q.n_max, 16, 20).lnz_per_site
-        got = ctx.run([H.params(q.beta, q.delta, q.n_max, 16, 20, prec=prec)])[0].lnz_per_site
+        got = ctx.run([H.params(q.beta, q.delta, q.n_max, 16, 20, prec=prec, block_sparse=bs)])[0].lnz_per_site
         errs.append(abs(got - ref))
     out["accuracy"] = {"max_abs_dlnz_vs_oracle": max(errs), "points": 3, "d_cut": 16, "n_steps": 20,
                        "note": "same (beta, Delta) points at D_cut=16 (oracle at D_cut=64 takes ~30 min/point)"}

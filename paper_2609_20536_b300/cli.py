@@ -1,6 +1,6 @@
 """Command-line entry points of the library.
 
-  python -m paper_2609_20536_b300.cli run --beta 1.1 --delta 0.5 --n-max 4 --d-cut 64 --steps 25 [--prec split]
+  python -m paper_2609_20536_b300.cli run --beta 1.1 --delta 0.5 --n-max 4 --d-cut 64 --steps 25 [--prec split] [--block-sparse 1]
   python -m paper_2609_20536_b300.cli contract --M 65536 --N 4096 --K 4096 [--prec split] [--repeat 1]
 
 `run` prints ln Z/N and the per-step scalars of one point; `contract` times
@@ -26,6 +26,7 @@ def main(argv=None):
     r.add_argument("--h", type=float, default=0.0)
     r.add_argument("--h1", type=float, default=0.0)
     r.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
+    r.add_argument("--block-sparse", type=int, default=1, choices=[0, 1])
     c = sub.add_parser("contract")
     c.add_argument("--M", type=int, required=True)
     c.add_argument("--N", type=int, required=True)
@@ -40,7 +41,8 @@ def main(argv=None):
     prec = {"split": H.SPLIT_BF16, "fast": H.SPLIT_BF16_FAST, "fp64": H.FP64}[a.prec]
     ctx = H.Context(stream=torch.cuda.current_stream().cuda_stream)
     if a.cmd == "run":
-        p = H.params(a.beta, a.delta, a.n_max, a.d_cut, a.steps, h=a.h, h1=a.h1, prec=prec)
+        p = H.params(a.beta, a.delta, a.n_max, a.d_cut, a.steps, h=a.h, h1=a.h1, prec=prec,
+                     block_sparse=a.block_sparse if prec != H.FP64 else 0)
         t0 = time.perf_counter()
         res = ctx.run([p])[0]
         dt = time.perf_counter() - t0

@@ -289,7 +289,7 @@ static hotrg_status environment_blocks(hotrg_ctx* ctx, int prec, int sym, const 
         const size_t mark = ctx->ws.used;
         BsPlan pl;
         hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_ENV, pl);
-        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, X, Y, C, PROF_GEMM_ENV);
+        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, X, 0, Y, 0, C, 0, PROF_GEMM_ENV);
         ctx->ws.used = mark;
         return st;
     };
@@ -403,11 +403,14 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
                                   const double* T_dn, double* W, double* Z, double* Tc, double* T_out) {
     const int64_t h = Dh, v = Dv, p = Dp, hh = h * h, vv = v * v;
     hotrg_status s;
-    auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const double* A, const double* B, double* C) {
+    // W and Z are written and read as exact FP32 pairs (8 bytes, the value hi + lo): the
+    // tensor-core epilogue then needs no FP64 arithmetic for these two largest outputs
+    auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const void* A, int af, const void* B,
+                   void* C, int cf) {
         const size_t mark = ctx->ws.used;
         BsPlan pl;
         hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl);
-        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, A, B, C, PROF_GEMM_COARSE);
+        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, A, af, B, 0, C, cf, PROF_GEMM_COARSE);
         ctx->ws.used = mark;
         return st;
     };
@@ -419,7 +422,7 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
         BsSet M{2, {{qn, p, +1, 1, hh * vv}, {qh, h, -1, p, v}}, p * h};
         BsSet K{1, {{qh, h, +1, h * p, h * vv}}, h};
         BsSet N{3, {{qh, h, +1, vv, v * h * v}, {qv, v, -1, v, h * v}, {qv, v, +1, 1, 1}}, h * vv};
-        if ((s = run(M, K, N, P, T_up, W)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, P, 0, T_up, W, 1)) != HOTRG_OK) return s;
     }
     // s2: Z[x][u][d][r1][r2] = sum_{l2,i} W[x][r1][u][l2][i] T_dn[l2][r2][i][d]
     {
@@ -427,7 +430,7 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
                 p * h * v};
         BsSet K{2, {{qh, h, +1, v, h * vv}, {qv, v, +1, 1, v}}, h * v};
         BsSet N{2, {{qv, v, +1, 1, hh}, {qh, h, +1, vv, 1}}, v * h};
-        if ((s = run(M, K, N, W, T_dn, Z)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, W, 1, T_dn, Z, 1)) != HOTRG_OK) return s;
     }
     // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][u][d][r1][r2] P[r1][r2][x']
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(Tc, 0, (size_t)p * vv * p * 8, ctx->stream));
@@ -435,7 +438,7 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
         BsSet M{3, {{qn, p, +1, vv * hh, vv * p}, {qv, v, +1, v * hh, v * p}, {qv, v, -1, hh, p}}, p * vv};
         BsSet K{2, {{qh, h, +1, h, h * p}, {qh, h, +1, 1, p}}, hh};
         BsSet N{1, {{qn, p, +1, 1, 1}}, p};
-        if ((s = run(M, K, N, Z, P, Tc)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, Z, 1, P, Tc, 0)) != HOTRG_OK) return s;
     }
     // relabel for the other axis: T_out[u][d][x][x'] = Tc[x][u][d][x']
     Perm po{4, {Dv, Dv, Dp, Dp}, {(int64_t)Dv * Dp, Dp, vv * Dp, 1}};

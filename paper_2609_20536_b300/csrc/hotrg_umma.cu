@@ -853,8 +853,10 @@ __device__ __forceinline__ int group_of_row(const BsGroup* gr, int G, int64_t r,
 }
 
 // One warp per padded slice row; rows beyond the plan's padded total leave at once.
+// X holds FP64 values (FMT_F64) or exact FP32 pairs hi + lo (FMT_F32PAIR).
+template <int FMT>
 __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
-    const double* __restrict__ X, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ koff,
+    const void* __restrict__ X, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ koff,
     const BsGroup* __restrict__ groups, const BsHeader* __restrict__ hdr, int b_side, int NS, int Kp,
     __nv_bfloat16* __restrict__ out, int64_t slice_stride, int32_t* __restrict__ exps) {
     extern __shared__ uint64_t srow_all[];
@@ -882,7 +884,9 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
     for (int k = lane; k < K; k += 32) {
         const uint64_t bits = ((const uint64_t*)X)[rbase + kof[k]];
         if (cached) srow[k] = bits;
-        emax = max(emax, exp_f64(__longlong_as_double((long long)bits)));
+        const int ex = FMT == FMT_F64 ? exp_f64(__longlong_as_double((long long)bits))
+                                      : exp_f32(__uint_as_float((uint32_t)(bits & 0xffffffffu)));
+        emax = max(emax, ex);
     }
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     __syncwarp();
@@ -893,9 +897,16 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
         int64_t F = 0;
         if (k < K && emax > -2000) {
             const uint64_t bits = cached ? srow[k] : ((const uint64_t*)X)[rbase + kof[k]];
-            const double d = __longlong_as_double((long long)bits);
-            const int64_t a = (int64_t)fixed_f64(d, T - e);
-            F = d < 0.0 ? -a : a;
+            if (FMT == FMT_F64) {
+                const int64_t a = (int64_t)fixed_f64(__longlong_as_double((long long)bits), T - e);
+                F = (bits >> 63) ? -a : a;  // the sign from the bit pattern (no FP64 compare)
+            } else {
+                const uint32_t hb = (uint32_t)(bits & 0xffffffffu), lb = (uint32_t)(bits >> 32);
+                const int G = 16;  // guard bits for the exact integer sum hi + lo
+                const int64_t fh = (int64_t)fixed_f32(__uint_as_float(hb), T - e + G) * ((hb >> 31) ? -1 : 1);
+                const int64_t fl = (int64_t)fixed_f32(__uint_as_float(lb), T - e + G) * ((lb >> 31) ? -1 : 1);
+                F = (fh + fl + (1ll << (G - 1))) >> G;
+            }
         }
         int64_t rem = F;
         for (int p = 0; p < NS; ++p) {
@@ -919,7 +930,7 @@ struct GroupArgs {
     const int32_t* eB;
     const int64_t* rowC;
     const int64_t* colC;
-    double* C;
+    void* C;
     int32_t* status;
 };
 
@@ -967,7 +978,7 @@ struct GroupCfg {
 // Persistent grouped GEMM: CTA b takes tiles b, b + gridDim.x, ...  The stage,
 // k-block and chunk counters run on across tiles, so the epilogue of one
 // tile (after its TMEM drain) overlaps the MMAs of the next.
-template <int NS>
+template <int NS, int OUT>
 __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
                                                                    GroupArgs args) {
@@ -1150,13 +1161,12 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             const int row_ok = my_lrow < gr.M ? 1 : 0;
             const int64_t my_roff = row_ok ? args.rowC[gr.mbase + my_lrow] : 0;
             const int my_ea = args.eA[gr.mpad + my_lrow];
-            double* stg = staging + (warp - 2) * (32 * Cfg::STG_LD);
+            float2* stg = (float2*)(staging + (warp - 2) * (32 * Cfg::STG_LD));
             const int cl = lane & 15;
 #pragma unroll
             for (int c0 = 0; c0 < 64; c0 += 16) {
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj)
-                    stg[lane * Cfg::STG_LD + jj] = (double)hi[c0 + jj] + (double)lo[c0 + jj];
+                for (int jj = 0; jj < 16; ++jj) stg[lane * Cfg::STG_LD + jj] = make_float2(hi[c0 + jj], lo[c0 + jj]);
                 __syncwarp();
                 const int lcol = tn * BN + colbase + c0 + cl;
                 const bool col_ok = lcol < gr.N;
@@ -1168,8 +1178,21 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                     const int64_t roff = __shfl_sync(0xffffffffu, my_roff, row);
                     const int ea = __shfl_sync(0xffffffffu, my_ea, row);
                     const int rok = __shfl_sync(0xffffffffu, row_ok, row);
-                    if (rok && col_ok)
-                        args.C[roff + coff] = ldexp(stg[row * Cfg::STG_LD + cl], ea + ceb - 2 * SLICE_B1);
+                    if (rok && col_ok) {
+                        const float2 v = stg[row * Cfg::STG_LD + cl];
+                        const int sc = ea + ceb - 2 * SLICE_B1;
+                        if (OUT == FMT_F32PAIR) {
+                            // exact pair, scaled in FP32 (no FP64 arithmetic in this epilogue)
+                            ((float2*)args.C)[roff + coff] = make_float2(ldexpf(v.x, sc), ldexpf(v.y, sc));
+                        } else {
+                            // FP64: the power-of-two scale is an add to the exponent field of the
+                            // (normal or zero) sum
+                            const double d = (double)v.x + (double)v.y;
+                            long long b = __double_as_longlong(d);
+                            if (b & 0x7ff0000000000000ll) b += (long long)sc << 52;
+                            ((double*)args.C)[roff + coff] = __longlong_as_double(b);
+                        }
+                    }
                 }
                 __syncwarp();
             }
@@ -1191,29 +1214,29 @@ size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN) {
     return (size_t)(5 * (rA + rB) * Kp * 2 + (rA + rB) * 4 + 4096);
 }
 
-template <int NS>
+template <int NS, int OUT>
 static hotrg_status launch_grouped(hotrg_ctx* ctx, const __nv_bfloat16* As, int64_t rA, const __nv_bfloat16* Bs,
                                    int64_t rB, int Kp, const GroupArgs& a, int prof_class) {
     using Cfg = GroupCfg<NS>;
     static bool attr = false;
     if (!attr) {
-        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 Cfg::SMEM));
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS, OUT>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
         attr = true;
     }
     CUtensorMap mA, mB;
     if (!make_map(&mA, As, NS, rA, Kp, BM) || !make_map(&mB, Bs, NS, rB, Kp, BN))
         return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
     const int h = prof_begin(ctx);
-    umma_grouped_kernel<NS><<<ctx->sm_count, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
+    umma_grouped_kernel<NS, OUT><<<ctx->sm_count, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
     prof_end(ctx, h, prof_class, 0.0);  // algorithmic flops are counted on the device by the planner
     HOTRG_COUNT(1);
     HOTRG_LAUNCH_CHECK(ctx, "umma_grouped_kernel");
     return HOTRG_OK;
 }
 
-hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const double* A, const double* B, double* C,
-                          int prof_class) {
+hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void* A, int afmt, const void* B,
+                          int bfmt, void* C, int cfmt, int prof_class) {
     if (!ctx->tc_ok) return set_err(ctx, HOTRG_ENOTSUP, "tensor-core engine needs sm_103");
     const int NS = ns_for(prec, prof_class == PROF_GEMM_COARSE);
     const int Kp = (int)round_up(pl.nK, BK);
@@ -1227,17 +1250,31 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const doub
     if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
     static bool attr = false;
     if (!attr) {
-        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel<FMT_F64>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 GATHER_WARPS * GATHER_SMEM_K * 8));
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel<FMT_F32PAIR>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  GATHER_WARPS * GATHER_SMEM_K * 8));
         attr = true;
     }
     cudaStream_t s = ctx->stream;
     const int smem = GATHER_WARPS * GATHER_SMEM_K * 8;
+    const unsigned gA = (unsigned)((rA + GATHER_WARPS - 1) / GATHER_WARPS);
+    const unsigned gB = (unsigned)((rB + GATHER_WARPS - 1) / GATHER_WARPS);
     const int h_slice = prof_begin(ctx);
-    slice_grouped_kernel<<<(unsigned)((rA + GATHER_WARPS - 1) / GATHER_WARPS), 32 * GATHER_WARPS, smem, s>>>(
-        A, pl.offM0, pl.offK0, pl.groups, pl.hdr, 0, NS, Kp, As, rA * Kp, eA);
-    slice_grouped_kernel<<<(unsigned)((rB + GATHER_WARPS - 1) / GATHER_WARPS), 32 * GATHER_WARPS, smem, s>>>(
-        B, pl.offN0, pl.offK1, pl.groups, pl.hdr, 1, NS, Kp, Bs, rB * Kp, eB);
+    if (afmt == FMT_F64)
+        slice_grouped_kernel<FMT_F64><<<gA, 32 * GATHER_WARPS, smem, s>>>(A, pl.offM0, pl.offK0, pl.groups, pl.hdr, 0,
+                                                                         NS, Kp, As, rA * Kp, eA);
+    else
+        slice_grouped_kernel<FMT_F32PAIR><<<gA, 32 * GATHER_WARPS, smem, s>>>(A, pl.offM0, pl.offK0, pl.groups,
+                                                                             pl.hdr, 0, NS, Kp, As, rA * Kp, eA);
+    if (bfmt == FMT_F64)
+        slice_grouped_kernel<FMT_F64><<<gB, 32 * GATHER_WARPS, smem, s>>>(B, pl.offN0, pl.offK1, pl.groups, pl.hdr, 1,
+                                                                         NS, Kp, Bs, rB * Kp, eB);
+    else
+        slice_grouped_kernel<FMT_F32PAIR><<<gB, 32 * GATHER_WARPS, smem, s>>>(B, pl.offN0, pl.offK1, pl.groups,
+                                                                             pl.hdr, 1, NS, Kp, Bs, rB * Kp, eB);
     HOTRG_COUNT(2);
     prof_end(ctx, h_slice, PROF_SLICE, 0.0);
     HOTRG_LAUNCH_CHECK(ctx, "slice_grouped_kernel");
@@ -1250,9 +1287,14 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const doub
     a.colC = pl.offN1;
     a.C = C;
     a.status = st;
-    if (NS == 5) return launch_grouped<5>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
-    if (NS == 4) return launch_grouped<4>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
-    return launch_grouped<3>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    if (cfmt == FMT_F32PAIR) {
+        if (NS == 5) return launch_grouped<5, FMT_F32PAIR>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        if (NS == 4) return launch_grouped<4, FMT_F32PAIR>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        return launch_grouped<3, FMT_F32PAIR>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    }
+    if (NS == 5) return launch_grouped<5, FMT_F64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    if (NS == 4) return launch_grouped<4, FMT_F64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    return launch_grouped<3, FMT_F64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
 }
 
 hotrg_status umma_check_status(hotrg_ctx* ctx) {

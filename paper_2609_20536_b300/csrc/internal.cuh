@@ -198,7 +198,8 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
                      BsPlan& out);
 size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN);
-hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const double* A, const double* B, double* C,
-                          int prof_class);
+// Operand / output formats: 0 = FP64, 1 = exact FP32 pairs (hi, lo) with value hi + lo.
+hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void* A, int afmt, const void* B,
+                          int bfmt, void* C, int cfmt, int prof_class);
 
 }  // namespace hotrg
