@@ -342,9 +342,9 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_sectors_kernel(const doubl
         double* rs = rc + cap;
         int* rp = (int*)(rs + cap);
         int* rq = rp + cap;
-        for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-            const int i = idx / m, j = idx % m;
-            A[idx] = E[(int64_t)w.members[start + i] * n + w.members[start + j]];
+        for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
+            const double* erow = E + (int64_t)w.members[start + i] * n;
+            for (int j = threadIdx.x & 31; j < m; j += 32) A[i * m + j] = erow[w.members[start + j]];
         }
         __syncthreads();
         const int sw = jacobi_block(A, V, m, max_sweeps, tol, rc, rs, rp, rq, red, &s_rot);
@@ -762,11 +762,13 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
         const int64_t aoff = w.sec_aoff[sct];
         float* Ef = (float*)(w.A[side] + aoff);
         double* E64 = w.S3[side] + aoff;
-        for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
-            const int i = (int)(idx / m), j = (int)(idx % m);
-            const double v = E[(int64_t)w.members[start + i] * n + w.members[start + j]];
-            E64[idx] = v;
-            Ef[idx] = (float)v;
+        for (int i = warp; i < m; i += nwarps) {  // rows by warps, columns by lanes (no 64-bit divides)
+            const double* erow = E + (int64_t)w.members[start + i] * n;
+            for (int j = lane; j < m; j += 32) {
+                const double v = erow[w.members[start + j]];
+                E64[(int64_t)i * m + j] = v;
+                Ef[(int64_t)i * m + j] = (float)v;
+            }
         }
         float* Q = sq;
         float* Y = sq + b * m;
@@ -775,25 +777,54 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
         __syncthreads();
         bcgs2_block(Q, m, b, 1u, 1e-3f, Rs, n0s);
         for (int it = 0; it < iters; ++it) {
-            for (int i = warp; i < m; i += nwarps) {
-                const float* er = Ef + (int64_t)i * m;
-                float acc[SUBF_BMAX];
+            // two rows of E_q per warp; each lane keeps 4 k values of both rows in flight
+            for (int i0 = 2 * warp; i0 < m; i0 += 2 * nwarps) {
+                const bool two = i0 + 1 < m;
+                const float* er0 = Ef + (int64_t)i0 * m;
+                const float* er1 = two ? er0 + m : er0;
+                float acc0[SUBF_BMAX], acc1[SUBF_BMAX];
 #pragma unroll
-                for (int j = 0; j < SUBF_BMAX; ++j) acc[j] = 0.f;
-                for (int k = lane; k < m; k += 32) {
-                    const float e = er[k];
-#pragma unroll
-                    for (int j = 0; j < SUBF_BMAX; ++j)
-                        if (j < b) acc[j] = fmaf(e, Q[j * m + k], acc[j]);
+                for (int j = 0; j < SUBF_BMAX; ++j) {
+                    acc0[j] = 0.f;
+                    acc1[j] = 0.f;
                 }
-                float mine = 0.f;
+                for (int k0 = lane; k0 < m; k0 += 128) {
+                    float e0[4], e1[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + 32 * u;
+                        e0[u] = k < m ? er0[k] : 0.f;
+                        e1[u] = k < m ? er1[k] : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + 32 * u;
+                        if (k < m) {
+#pragma unroll
+                            for (int j = 0; j < SUBF_BMAX; ++j)
+                                if (j < b) {
+                                    const float q = Q[j * m + k];
+                                    acc0[j] = fmaf(e0[u], q, acc0[j]);
+                                    acc1[j] = fmaf(e1[u], q, acc1[j]);
+                                }
+                        }
+                    }
+                }
+                float mine0 = 0.f, mine1 = 0.f;
 #pragma unroll
                 for (int j = 0; j < SUBF_BMAX; ++j)
                     if (j < b) {
-                        const float v = warp_sum_f(acc[j]);
-                        if (lane == j) mine = v;
+                        const float v0 = warp_sum_f(acc0[j]);
+                        const float v1 = warp_sum_f(acc1[j]);
+                        if (lane == j) {
+                            mine0 = v0;
+                            mine1 = v1;
+                        }
                     }
-                if (lane < b) Y[lane * m + i] = mine;
+                if (lane < b) {
+                    Y[lane * m + i0] = mine0;
+                    if (two) Y[lane * m + i0 + 1] = mine1;
+                }
             }
             __syncthreads();
             bcgs2_block(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, Rs, n0s);

@@ -853,7 +853,9 @@ __device__ __forceinline__ int group_of_row(const BsGroup* gr, int G, int64_t r,
 }
 
 // One warp per padded slice row; rows beyond the plan's padded total leave at once.
-// X holds FP64 values (FMT_F64) or exact FP32 pairs hi + lo (FMT_F32PAIR).
+// X holds FP64 values (FMT_F64) or exact FP32 pairs hi + lo (FMT_F32PAIR).  Rows
+// of up to GROUP_SMEM_K elements are read once (4 KB of shared memory per warp).
+constexpr int GROUP_SMEM_K = 512;
 template <int FMT>
 __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
     const void* __restrict__ X, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ koff,
@@ -878,15 +880,27 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
         return;
     }
     const int64_t rbase = rowoff[(b_side ? gr.nbase : gr.mbase) + local];
-    const bool cached = K <= GATHER_SMEM_K;
-    uint64_t* srow = srow_all + (size_t)wib * GATHER_SMEM_K;
+    const bool cached = K <= GROUP_SMEM_K;
+    uint64_t* srow = srow_all + (size_t)wib * GROUP_SMEM_K;
     int emax = -2000;
-    for (int k = lane; k < K; k += 32) {
-        const uint64_t bits = ((const uint64_t*)X)[rbase + kof[k]];
-        if (cached) srow[k] = bits;
-        const int ex = FMT == FMT_F64 ? exp_f64(__longlong_as_double((long long)bits))
-                                      : exp_f32(__uint_as_float((uint32_t)(bits & 0xffffffffu)));
-        emax = max(emax, ex);
+    // four elements per lane in flight: offsets first, then the values they point at
+    for (int k0 = lane; k0 < K; k0 += 128) {
+        int64_t o[4];
+        uint64_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[u] = k0 + 32 * u < K ? kof[k0 + 32 * u] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = k0 + 32 * u < K ? ((const uint64_t*)X)[rbase + o[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + 32 * u;
+            if (k < K) {
+                if (cached) srow[k] = v[u];
+                const int ex = FMT == FMT_F64 ? exp_f64(__longlong_as_double((long long)v[u]))
+                                              : exp_f32(__uint_as_float((uint32_t)(v[u] & 0xffffffffu)));
+                emax = max(emax, ex);
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     __syncwarp();
@@ -1252,14 +1266,14 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
     if (!attr) {
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel<FMT_F64>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 GATHER_WARPS * GATHER_SMEM_K * 8));
+                                                 GATHER_WARPS * GROUP_SMEM_K * 8));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel<FMT_F32PAIR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 GATHER_WARPS * GATHER_SMEM_K * 8));
+                                                 GATHER_WARPS * GROUP_SMEM_K * 8));
         attr = true;
     }
     cudaStream_t s = ctx->stream;
-    const int smem = GATHER_WARPS * GATHER_SMEM_K * 8;
+    const int smem = GATHER_WARPS * GROUP_SMEM_K * 8;
     const unsigned gA = (unsigned)((rA + GATHER_WARPS - 1) / GATHER_WARPS);
     const unsigned gB = (unsigned)((rB + GATHER_WARPS - 1) / GATHER_WARPS);
     const int h_slice = prof_begin(ctx);
