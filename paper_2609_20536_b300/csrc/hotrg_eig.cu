@@ -840,25 +840,74 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
 }
 
 // FP64 basis: Q64 = CGS2(double(Q32)), in S2.
+// FP64 basis from the FP32 one: Q64 = double(Q32) R^-1 with R the Cholesky
+// factor of G = Q64^T Q64 (one Cholesky QR).  The FP32 basis is orthonormal
+// to ~1e-7, so G is within ~1e-7 of the identity and one pass leaves Q64
+// orthonormal to rounding.  A column whose pivot falls below 1e-8 of its
+// diagonal (a column the FP32 stage zeroed, or a dependent one) is set to
+// zero and dropped from the factorisation.  Result in S2, m x b row-major.
 __global__ void __launch_bounds__(SUB_THREADS) rr_prep_kernel(EigWs w) {
-    __shared__ double rbuf[BCAP_MAX];
-    __shared__ double red[40];
+    extern __shared__ double G[];  // bcap x bcap, sized at launch
+    __shared__ int live[BCAP_MAX];
     const int side = blockIdx.y;
     const int nsec = *w.nsec;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
         const int m = w.sec_start[sct + 1] - w.sec_start[sct];
         const int b = w.sec_b[sct];
         if (b == m) continue;
         const int64_t aoff = w.sec_aoff[sct];
-        const float* Q32 = (const float*)(w.S1[side] + aoff);
+        const float* Q32 = (const float*)(w.S1[side] + aoff);  // b x m (transposed)
         double* Q = w.S2[side] + aoff;
-        // Q32 is stored transposed (b x m)
-        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) {
-            const int t = (int)(idx / b), j = (int)(idx % b);
-            Q[idx] = (double)Q32[(int64_t)j * m + t];
+        for (int t = warp; t < m; t += nw)
+            for (int j = lane; j < b; j += 32) Q[(int64_t)t * b + j] = (double)Q32[(int64_t)j * m + t];
+        __syncthreads();
+        // G = Q^T Q (upper triangle, one dot product per warp task)
+        for (int task = warp; task < b * b; task += nw) {
+            const int i = task / b, j = task % b;
+            if (i > j) continue;
+            double a = 0.0;
+            for (int t = lane; t < m; t += 32) a = fma(Q[(int64_t)t * b + i], Q[(int64_t)t * b + j], a);
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) {
+                G[i * b + j] = a;
+                G[j * b + i] = a;
+            }
         }
         __syncthreads();
-        cgs2<double>(Q, m, b, rbuf, red, 100003u, 1e-8);
+        // in-place Cholesky G = R^T R (R upper, stored in G's upper triangle), one warp
+        if (warp == 0) {
+            for (int j = 0; j < b; ++j) {
+                const double d = G[j * b + j];
+                __syncwarp();
+                const bool ok = d > 1e-8;  // unit-norm columns: d ~ 1 unless dependent or zeroed
+                if (lane == 0) live[j] = ok ? 1 : 0;
+                const double rjj = ok ? sqrt(d) : 1.0;
+                for (int c = j + lane; c < b; c += 32) G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] / rjj) : (c == j ? 1.0 : 0.0);
+                __syncwarp();
+                // trailing update: G[r][c] -= R[j][r] R[j][c] for j < r <= c
+                for (int idx = lane; idx < b * b; idx += 32) {
+                    const int r = idx / b, c = idx % b;
+                    if (r > j && c >= r) G[r * b + c] -= G[j * b + r] * G[j * b + c];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        // Q <- Q R^-1 row by row (forward substitution x R = q); dropped columns become zero
+        for (int t = tid; t < m; t += blockDim.x) {
+            double* q = Q + (int64_t)t * b;  // in place: q[i], i < j, already holds x_i
+            for (int j = 0; j < b; ++j) {
+                if (!live[j]) {
+                    q[j] = 0.0;
+                    continue;
+                }
+                double a = q[j];
+                for (int i = 0; i < j; ++i) a = fma(-q[i], G[i * b + j], a);
+                q[j] = a / G[j * b + j];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1170,6 +1219,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
                                                  (int)RR_SMEM_BYTES));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(subspace_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  SUBF_SMEM));
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 BCAP_MAX * BCAP_MAX * (int)sizeof(double)));
         g_attr_done = true;
     }
     EigWs w = carve(ws, n);
@@ -1224,7 +1275,7 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         prof_end(ctx, hp1, PROF_EIG_PART0 + 1, 0.0);
         HOTRG_LAUNCH_CHECK(ctx, "subspace_fp32_kernel");
         const int hp2 = prof_begin(ctx);
-        rr_prep_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(w);
+        rr_prep_kernel<<<dim3(sgrid, sides), SUB_THREADS, (size_t)bcap * bcap * sizeof(double), st>>>(w);
         HOTRG_LAUNCH_CHECK(ctx, "rr_prep_kernel");
         const int tiles = (n + GB_ROWS - 1) / GB_ROWS;
         rr_product_kernel<<<dim3(tiles < 64 ? tiles : 64, sgrid < 32 ? sgrid : 32, sides), 256, 0, st>>>(w);
