@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--points", type=int, default=2, help="points per bench step per GPU")
-    ap.add_argument("--nstreams", type=int, default=2,
-                    help="worker streams of the batch runner (1: points one after another on one stream)")
+    ap.add_argument("--nstreams", type=int, default=0,
+                    help="worker streams of the batch runner (0: autotuned over 1..3 before the warm-up; "
+                         "1: points one after another on one stream)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     ap.add_argument("--block-sparse", type=int, default=1, choices=[0, 1],
@@ -240,6 +241,13 @@ def main():
         return [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec, block_sparse=args.block_sparse)
                 for p in pts[base:base + P]]
 
+    tuned = None
+    if args.nstreams == 0:
+        # autotune the worker-stream count on one bench step's worth of points (untimed)
+        best, secs = ctx.autotune_batch(batch(0), max_streams=3)
+        tuned = {"chosen": best, "seconds_per_count": secs, "points": P}
+        args.nstreams = best
+
     def run(plist):
         if args.nstreams > 1:
             return ctx.run_batch(plist, nstreams=args.nstreams)
@@ -310,7 +318,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec != H.FP64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD + (WORKLOAD_BS if args.block_sparse else ""), "points_per_step": P, "worker_streams": args.nstreams,
+            "config": {"workload": WORKLOAD + (WORKLOAD_BS if args.block_sparse else ""), "points_per_step": P,
+                       "worker_streams": args.nstreams, "autotune": tuned,
                        "d_cut": D_CUT, "n_max": N_MAX,
                        "n_steps": N_STEPS, "prec": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "working set above L2: 8.6 GB D^5 intermediates per HOTRG step"},

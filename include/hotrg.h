@@ -198,10 +198,21 @@ hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoin
  * recorded on it bracket the batch.  With profiling on (hotrg_profile_enable)
  * no graph is replayed: every point runs directly, its regions are timed on
  * its worker's stream and added to the context's counters.
+ * nstreams = 0 takes the count chosen by hotrg_autotune_batch (2 if untuned).
  * params, out: host arrays of npoints.  Synchronous.  Returns the first
  * non-OK status (each out[i].status holds its own). */
 hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
                              int32_t imp_kind, int32_t nstreams, hotrg_result* out);
+
+/* Autotuner of the batch runner (no counterpart in the thesis): runs the
+ * sample points (host array, pure tensors) through hotrg_run_batch with 1,
+ * 2, ..., max_streams (<= 16) worker streams, each once untimed (workspaces,
+ * graphs) and once timed on the host clock, and keeps the fastest count in
+ * the context; hotrg_run_batch and hotrg_observables_batch with nstreams = 0
+ * use it (2 when never tuned).  best (may be NULL) receives the choice,
+ * seconds (may be NULL, max_streams entries) the timed runs.  Synchronous. */
+hotrg_status hotrg_autotune_batch(hotrg_ctx* ctx, const hotrg_params* sample, int32_t npoints,
+                                  int32_t max_streams, int32_t* best, double* seconds);
 
 /* Observables of npoints points (§3.4): ln Z/N and f at zero field;
  * C_V = beta^2 [l(beta+hb) - 2 l(beta) + l(beta-hb)] / hb^2 (Eq. 3.17);
@@ -215,7 +226,7 @@ hotrg_status hotrg_observables(hotrg_ctx* ctx, const hotrg_params* params, int32
 /* hotrg_observables for many points at once: the nine runs of every point
  * (beta, beta +- hb; h = hbar, hbar +- dh with the M impurity; h1 = hbar,
  * hbar +- dh with the M1 impurity) go through hotrg_run_batch on nstreams
- * worker streams (1..16), so the outputs equal hotrg_observables' bit for
+ * worker streams (1..16; 0: the autotuned count), so the outputs equal hotrg_observables' bit for
  * bit.  Synchronous.  Returns the first failing run's status (each out[i]
  * holds its own); HOTRG_EINVAL for bad arguments. */
 hotrg_status hotrg_observables_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,

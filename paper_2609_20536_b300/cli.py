@@ -2,10 +2,13 @@
 
   python -m paper_2609_20536_b300.cli run --beta 1.1 --delta 0.5 --n-max 4 --d-cut 64 --steps 25 [--prec split] [--block-sparse 1]
   python -m paper_2609_20536_b300.cli contract --M 65536 --N 4096 --K 4096 [--prec split] [--repeat 1]
+  python -m paper_2609_20536_b300.cli grid --n 64 [--nstreams 0]
 
-`run` prints ln Z/N and the per-step scalars of one point; `contract` times
-one C = A B^T of the given shape through the contraction engine (random
-FP64 operands generated on the device).
+`run` prints ln Z/N and the per-step scalars of one point; `grid` times a
+sample of the 64 x 64 (beta, Delta) grid with D_cut drawn from {24, 32, 48,
+64} through the batch runner; `contract` times one C = A B^T of the given
+shape through the contraction engine (random FP64 operands generated on the
+device).
 """
 
 import argparse
@@ -27,6 +30,12 @@ def main(argv=None):
     r.add_argument("--h1", type=float, default=0.0)
     r.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     r.add_argument("--block-sparse", type=int, default=1, choices=[0, 1])
+    g = sub.add_parser("grid")
+    g.add_argument("--n", type=int, default=64, help="first n points of the 64 x 64 (beta, Delta) grid")
+    g.add_argument("--stride", type=int, default=61, help="take every stride-th grid point (spreads beta, Delta)")
+    g.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
+    g.add_argument("--block-sparse", type=int, default=1, choices=[0, 1])
+    g.add_argument("--nstreams", type=int, default=0, help="0: autotune 1..4 worker streams on 8 points first")
     c = sub.add_parser("contract")
     c.add_argument("--M", type=int, required=True)
     c.add_argument("--N", type=int, required=True)
@@ -49,6 +58,26 @@ def main(argv=None):
         print(json.dumps({"lnz_per_site": res.lnz_per_site, "seconds": dt,
                           "ln_c": [res.step[k].ln_c for k in range(a.steps)],
                           "side": [res.step[k].side for k in range(a.steps)]}))
+    elif a.cmd == "grid":
+        from .workloads import grid_points
+        allp = grid_points()
+        sel = [allp[(i * a.stride) % len(allp)] for i in range(a.n)]
+        bs = a.block_sparse if prec != H.FP64 else 0
+        plist = [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec, block_sparse=bs) for p in sel]
+        tuned = None
+        if a.nstreams == 0:
+            best, secs = ctx.autotune_batch(plist[:8], max_streams=4)
+            tuned = {"chosen": best, "seconds_per_count": secs}
+        ctx.run_batch(plist[:4], nstreams=a.nstreams)  # workspaces and graphs of the classes
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.run_batch(plist, nstreams=a.nstreams)
+        dt = time.perf_counter() - t0
+        counts = {}
+        for p in sel:
+            counts[p.d_cut] = counts.get(p.d_cut, 0) + 1
+        print(json.dumps({"points": a.n, "seconds": dt, "points_per_s": a.n / dt, "d_cut_counts": counts,
+                          "autotune": tuned, "status": sorted(set(r.status for r in res))}))
     else:
         g = torch.Generator(device="cuda").manual_seed(0)
         A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <vector>
 
@@ -196,8 +197,12 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
                                   {(int64_t)Dp * Dh * Dv, (int64_t)hv, (int64_t)hv},
                                   {(int64_t)Dp * Dv * Dv, (int64_t)Dp, (int64_t)n}};
     size_t g = 0;
-    for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
-    if (p->block_sparse && p->prec != HOTRG_FP64) {
+    // the dense engine is needed unless every product of the step runs per block (the same
+    // condition as do_step's)
+    const bool blocks = p->block_sparse && p->prec != HOTRG_FP64 && !imp && sym_of(p) != SYM_NONE;
+    if (!blocks)
+        for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
+    if (blocks) {
         // grouped products: (M, K, N) of s1, s2, s3 and of the environments' A, B and E
         const int64_t gs[5][3] = {{(int64_t)Dp * Dh, Dh, (int64_t)Dh * Dv * Dv},
                                   {(int64_t)Dp * Dh * Dv, (int64_t)hv, (int64_t)hv},
@@ -205,7 +210,8 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
                                   {(int64_t)hv, (int64_t)hv, (int64_t)hv},
                                   {(int64_t)n, (int64_t)Dv * Dv, (int64_t)n}};
         for (auto& sh : gs)
-            g = std::max(g, bs_plan_bytes(sh[0], sh[1], sh[2]) + umma_grouped_workspace(sh[0], sh[1], sh[2]) + 4096);
+            g = std::max(g, bs_plan_bytes(sh[0], sh[1], sh[2]) +
+                                umma_grouped_workspace(sh[0], sh[1], sh[2], sym_of(p)) + 4096);
     }
     b += g;
     return b;
@@ -982,7 +988,8 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
     if (!ctx) return HOTRG_EINVAL;
     ctx->last_error.clear();
     if (!params || !out || npoints < 0) return set_err(ctx, HOTRG_EINVAL, "bad arguments");
-    if (nstreams < 1 || nstreams > 16) return set_err(ctx, HOTRG_EINVAL, "nstreams must lie in [1, 16]");
+    if (nstreams == 0) nstreams = ctx->tuned_streams > 0 ? ctx->tuned_streams : 2;
+    if (nstreams < 1 || nstreams > 16) return set_err(ctx, HOTRG_EINVAL, "nstreams must lie in [0, 16]");
     if (imp_kind != HOTRG_T_PURE && imp_kind != HOTRG_T_IMP_M && imp_kind != HOTRG_T_IMP_M1)
         return set_err(ctx, HOTRG_EINVAL, "imp_kind must be PURE, IMP_M or IMP_M1");
     hotrg_status first = HOTRG_OK;
@@ -1252,7 +1259,7 @@ hotrg_status hotrg_observables_batch(hotrg_ctx* ctx, const hotrg_params* params,
     ctx->last_error.clear();
     if (!params || !out || npoints < 0 || !(hb > 0) || !(hbar >= 0) || !(dh > 0) || hbar - dh < 0)
         return set_err(ctx, HOTRG_EINVAL, "bad arguments (need hb > 0, dh > 0, hbar >= dh)");
-    if (nstreams < 1 || nstreams > 16) return set_err(ctx, HOTRG_EINVAL, "nstreams must lie in [1, 16]");
+    if (nstreams < 0 || nstreams > 16) return set_err(ctx, HOTRG_EINVAL, "nstreams must lie in [0, 16]");
     for (int i = 0; i < npoints; ++i) memset(&out[i], 0, sizeof(hotrg_obs));
     if (npoints == 0) return HOTRG_OK;
     // three families (beta +-hb pure; h = hbar +-dh with the M impurity; h1 = hbar +-dh with the M1
@@ -1307,6 +1314,35 @@ hotrg_status hotrg_observables_batch(hotrg_ctx* ctx, const hotrg_params* params,
     }
     if (fatal != HOTRG_OK) ctx->last_error = fatal_msg;
     return fatal;
+}
+
+
+hotrg_status hotrg_autotune_batch(hotrg_ctx* ctx, const hotrg_params* sample, int32_t npoints, int32_t max_streams,
+                                  int32_t* best, double* seconds) {
+    if (!ctx) return HOTRG_EINVAL;
+    ctx->last_error.clear();
+    if (!sample || npoints < 1 || max_streams < 1 || max_streams > 16)
+        return set_err(ctx, HOTRG_EINVAL, "need npoints >= 1 and max_streams in [1, 16]");
+    std::vector<hotrg_result> res((size_t)npoints);
+    double tbest = 0.0;
+    int kbest = 0;
+    for (int k = 1; k <= max_streams; ++k) {
+        // one untimed pass builds the workers' workspaces and graphs, the second is timed
+        hotrg_status s = hotrg_run_batch(ctx, sample, npoints, HOTRG_T_PURE, k, res.data());
+        if (s != HOTRG_OK) return s;
+        const auto t0 = std::chrono::steady_clock::now();
+        s = hotrg_run_batch(ctx, sample, npoints, HOTRG_T_PURE, k, res.data());
+        if (s != HOTRG_OK) return s;
+        const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (seconds) seconds[k - 1] = t;
+        if (kbest == 0 || t < tbest) {
+            tbest = t;
+            kbest = k;
+        }
+    }
+    ctx->tuned_streams = kbest;
+    if (best) *best = kbest;
+    return HOTRG_OK;
 }
 
 }  // extern "C"

@@ -16,6 +16,8 @@
 // For every position it stores the two element offsets the engine needs
 // (operand and output for M and N, A and B for K).  Groups whose value has
 // no element of K still get tiles: their block of C is zero and is written.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace hotrg {
@@ -76,7 +78,8 @@ __global__ void __launch_bounds__(BS_V) bs_scan_kernel(const int32_t* __restrict
                                                        const int32_t* __restrict__ cN, int64_t nN,
                                                        int32_t* __restrict__ sM, int32_t* __restrict__ sK,
                                                        int32_t* __restrict__ sN, BsGroup* __restrict__ groups,
-                                                       BsHeader* __restrict__ hdr, double* flops_acc) {
+                                                       BsHeader* __restrict__ hdr, double* flops_acc, int kp_cap,
+                                                       int32_t* status) {
     __shared__ int64_t tot[3][BS_V], base[3][BS_V];
     const int v = threadIdx.x;
     const int32_t* cs[3] = {cM, cK, cN};
@@ -118,6 +121,11 @@ __global__ void __launch_bounds__(BS_V) bs_scan_kernel(const int32_t* __restrict
             g.K = (int32_t)tot[1][u];
             g.N = (int32_t)tot[2][u];
             g.Kp = (g.K + 31) / 32 * 32;
+            if (g.Kp > kp_cap) {  // the slice pitch is too small for this block: fail the run, touch nothing
+                atomicExch(status, (int)HOTRG_ENOTSUP);
+                g.Kp = 0;
+                g.K = 0;
+            }
             g.mpad = mpad;
             g.npad = npad;
             g.tiles_n = (g.N + 127) / 128;
@@ -207,8 +215,11 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
         bs_count_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, counts[i], nch[i], st);
     }
     double* facc = (ctx->prof.on && ctx->prof.dflops) ? ctx->prof.dflops + prof_class : nullptr;
+    // slice pitch: the whole K set for small sets and Z2 (two blocks); half of it for larger U(1)
+    // sets, whose blocks hold a small fraction of K (the device checks every block against it)
+    out.kp_cap = bs_pitch(K.size, sym);
     bs_scan_kernel<<<1, BS_V, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
-                                      starts[2], out.groups, out.hdr, facc);
+                                      starts[2], out.groups, out.hdr, facc, out.kp_cap, st);
     for (int i = 0; i < 3; ++i) {
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
         bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], offs[i][0], offs[i][1]);

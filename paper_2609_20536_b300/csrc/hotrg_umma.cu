@@ -32,6 +32,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
@@ -1222,8 +1223,13 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
     if (threadIdx.x == 0 && *s_fail) atomicExch(args.status, (int)HOTRG_ETIMEOUT);
 }
 
-size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN) {
-    const int64_t Kp = round_up(nK, BK);
+int32_t bs_pitch(int64_t nK, int sym) {
+    const int64_t kfull = round_up(nK, BK);
+    return (int32_t)((sym == SYM_U1 && kfull > 4096) ? std::max<int64_t>(4096, round_up(kfull / 2, BK)) : kfull);
+}
+
+size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN, int sym) {
+    const int64_t Kp = bs_pitch(nK, sym);
     const int64_t rA = round_up(nM, BM) + (int64_t)BS_V * BM, rB = round_up(nN, BN) + (int64_t)BS_V * BN;
     return (size_t)(5 * (rA + rB) * Kp * 2 + (rA + rB) * 4 + 4096);
 }
@@ -1253,7 +1259,7 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
                           int bfmt, void* C, int cfmt, int prof_class) {
     if (!ctx->tc_ok) return set_err(ctx, HOTRG_ENOTSUP, "tensor-core engine needs sm_103");
     const int NS = ns_for(prec, prof_class == PROF_GEMM_COARSE);
-    const int Kp = (int)round_up(pl.nK, BK);
+    const int Kp = pl.kp_cap;  // slice row pitch, a multiple of 32
     const int64_t rA = round_up(pl.nM, BM) + (int64_t)BS_V * BM, rB = round_up(pl.nN, BN) + (int64_t)BS_V * BN;
     __nv_bfloat16* As = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * rA * Kp * 2);
     __nv_bfloat16* Bs = (__nv_bfloat16*)ws_alloc(ctx, (size_t)NS * rB * Kp * 2);

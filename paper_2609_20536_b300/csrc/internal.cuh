@@ -57,6 +57,7 @@ struct hotrg_ctx {
     bool tc_ok = false;  // sm_103a tensor-core path usable on this device
     hotrg::Profiler prof;
     void* batch = nullptr;  // worker streams and graph cache of hotrg_run_batch
+    int tuned_streams = 0;  // hotrg_autotune_batch's choice (0: not tuned, batch calls default to 2)
 };
 
 namespace hotrg {
@@ -190,6 +191,7 @@ struct BsPlan {  // device pointers (workspace) plus the host-known set sizes
     int64_t *offK0, *offK1;  // K set: offsets in A, in B
     int64_t *offN0, *offN1;  // N set: offsets in B, in C
     int64_t nM, nK, nN;
+    int32_t kp_cap;  // slice row pitch (>= every block's padded K; checked on the device)
 };
 size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // Enqueues the planner for C = A B^T over index sets (M, K, N) with the given
@@ -197,7 +199,10 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // status word.
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
                      BsPlan& out);
-size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN);
+// Slice row pitch of a grouped product: the whole K set rounded to 32 for small sets and
+// Z2; half of it (at least 4096) for larger U(1) sets (bs_plan checks every block on the device).
+int32_t bs_pitch(int64_t nK, int sym);
+size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN, int sym);
 // Operand / output formats: 0 = FP64, 1 = exact FP32 pairs (hi, lo) with value hi + lo.
 hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void* A, int afmt, const void* B,
                           int bfmt, void* C, int cfmt, int prof_class);

@@ -196,6 +196,20 @@ def hotrg_run_batch(ctx, plist, imp_kind=T_PURE, nstreams=2, check=True):
     return list(out)
 
 
+def hotrg_autotune_batch(ctx, plist, max_streams=4):
+    """Times hotrg_run_batch with 1..max_streams worker streams; returns (best, seconds per count)."""
+    n = len(plist)
+    arr = (Params * n)(*plist)
+    best = ctypes.c_int32(0)
+    secs = (ctypes.c_double * max_streams)()
+    f = lib.hotrg_autotune_batch
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32,
+                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    _check(ctx, f(ctx, arr, n, max_streams, ctypes.byref(best), secs))
+    return best.value, list(secs)
+
+
 def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
     n = len(plist)
     arr = (Params * n)(*plist)
@@ -439,6 +453,9 @@ class Context:
 
     def run_batch(self, plist, imp_kind=T_PURE, nstreams=2):
         return hotrg_run_batch(self.handle, plist, imp_kind, nstreams)
+
+    def autotune_batch(self, plist, max_streams=4):
+        return hotrg_autotune_batch(self.handle, plist, max_streams)
 
     def observables(self, plist, hb=1e-3, hbar=0.01, dh=1e-3):
         return hotrg_observables(self.handle, plist, hb, hbar, dh)

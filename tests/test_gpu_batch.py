@@ -70,3 +70,12 @@ def test_batch_with_profiling_equals_graph_replay(H, C):
     assert got == replay
     assert prof.steps == sum(p.n_steps for p in pts)
     assert prof.gemm_calls[1] > 0 and prof.gemm_ms[1] > 0 and prof.eig_ms > 0
+
+
+def test_autotune_batch_and_tuned_stream_count(H, C):
+    pts = points(H, H.SPLIT_BF16)[:4]
+    best, secs = C.autotune_batch(pts, max_streams=3)
+    assert 1 <= best <= 3 and len(secs) == 3 and all(t > 0 for t in secs)
+    single = [C.run([p])[0].lnz_per_site for p in pts]
+    got = [r.lnz_per_site for r in C.run_batch(pts, nstreams=0)]  # 0: the tuned count
+    assert got == single
