@@ -3,10 +3,13 @@
   python -m paper_2609_20536_b300.cli run --beta 1.1 --delta 0.5 --n-max 4 --d-cut 64 --steps 25 [--prec split] [--block-sparse 1]
   python -m paper_2609_20536_b300.cli contract --M 65536 --N 4096 --K 4096 [--prec split] [--repeat 1]
   python -m paper_2609_20536_b300.cli grid --n 64 [--nstreams 0]
+  python -m paper_2609_20536_b300.cli surrogate [--nb 12 --nd 8 --d-cut 12 --steps 16]
 
 `run` prints ln Z/N and the per-step scalars of one point; `grid` times a
 sample of the 64 x 64 (beta, Delta) grid with D_cut drawn from {24, 32, 48,
-64} through the batch runner; `contract` times one C = A B^T of the given
+64} through the batch runner; `surrogate` builds a training grid of
+observables, trains the MLP ensemble, audits it against HOTRG on random
+points and refines near the C_V / chi maxima; `contract` times one C = A B^T of the given
 shape through the contraction engine (random FP64 operands generated on the
 device).
 """
@@ -36,6 +39,16 @@ def main(argv=None):
     g.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     g.add_argument("--block-sparse", type=int, default=1, choices=[0, 1])
     g.add_argument("--nstreams", type=int, default=0, help="0: autotune 1..4 worker streams on 8 points first")
+    sg = sub.add_parser("surrogate")
+    sg.add_argument("--nb", type=int, default=12, help="training grid: nb betas in [0.6, 1.6]")
+    sg.add_argument("--nd", type=int, default=8, help="training grid: nd Deltas in [0.1, 0.9]")
+    sg.add_argument("--n-max", type=int, default=2)
+    sg.add_argument("--d-cut", type=int, default=12)
+    sg.add_argument("--steps", type=int, default=16)
+    sg.add_argument("--epochs", type=int, default=2000)
+    sg.add_argument("--threshold", type=float, default=1e-3)
+    sg.add_argument("--audit", type=int, default=64)
+    sg.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     c = sub.add_parser("contract")
     c.add_argument("--M", type=int, required=True)
     c.add_argument("--N", type=int, required=True)
@@ -78,6 +91,42 @@ def main(argv=None):
             counts[p.d_cut] = counts.get(p.d_cut, 0) + 1
         print(json.dumps({"points": a.n, "seconds": dt, "points_per_s": a.n / dt, "d_cut_counts": counts,
                           "autotune": tuned, "status": sorted(set(r.status for r in res))}))
+    elif a.cmd == "surrogate":
+        import numpy as np
+        out = {}
+
+        def mk(b, d):
+            return H.params(b, d, a.n_max, a.d_cut, a.steps, prec=prec, block_sparse=1 if prec != H.FP64 else 0)
+
+        betas, deltas = np.linspace(0.6, 1.6, a.nb), np.linspace(0.1, 0.9, a.nd)
+        X = np.array([[b, d] for d in deltas for b in betas])
+        t0 = time.perf_counter()
+        obs = ctx.observables_batch([mk(b, d) for b, d in X], nstreams=0)
+        out["train_points"], out["train_observables_s"] = len(X), time.perf_counter() - t0
+        Y = np.array([[o.f, o.cv, o.chi, o.chi1] for o in obs])
+        sur = H.Surrogate(ensemble=4, seed=20536)
+        t0 = time.perf_counter()
+        out["final_loss"] = sur.fit(X, Y, epochs=a.epochs, batch=64, lr=2e-3)
+        out["fit_s"] = time.perf_counter() - t0
+        rng = np.random.default_rng(7)
+        Xa = np.column_stack([rng.uniform(0.6, 1.6, a.audit), rng.uniform(0.1, 0.9, a.audit)])
+        t0 = time.perf_counter()
+        pred, sd = sur.predict(Xa)
+        out["predictions_per_s"] = len(Xa) / (time.perf_counter() - t0)
+        ref = ctx.observables_batch([mk(b, d) for b, d in Xa], nstreams=0)
+        R = np.array([[o.f, o.cv, o.chi, o.chi1] for o in ref])
+        err = np.abs(pred - R) / np.array(sur.scaling.y_std[:])
+        out["audit_std_err_max"] = err.max(0).tolist()
+        out["audit_std_err_rms"] = np.sqrt((err ** 2).mean(0)).tolist()
+        out["audit_spread_median"] = float(np.median(sd.max(1)))
+        Xr, pk = sur.peaks(deltas, 0.6, 1.6, 201, 4, 0.05)
+        t0 = time.perf_counter()
+        _, _, solved = sur.refine(ctx, mk(1.0, 0.5), Xr, threshold=a.threshold, nstreams=0)
+        out["refine_points"], out["refine_resolved"] = len(Xr), int(solved.sum())
+        out["refine_s"] = time.perf_counter() - t0
+        out["peak_beta_cv_chi"] = pk.tolist()
+        sur.close()
+        print(json.dumps(out))
     else:
         g = torch.Generator(device="cuda").manual_seed(0)
         A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)

@@ -58,7 +58,7 @@ def test_observables_batch_rejects_bad_arguments(H, C):
     with pytest.raises(H.HotrgError):
         C.observables_batch([H.params(1.0, 0.5, 2, 8, 4)], hbar=0.0, dh=1e-3)
     with pytest.raises(H.HotrgError):
-        C.observables_batch([H.params(1.0, 0.5, 2, 8, 4)], nstreams=0)
+        C.observables_batch([H.params(1.0, 0.5, 2, 8, 4)], nstreams=17)  # 0 means the autotuned count
 
 
 def oracle_members(sur):
