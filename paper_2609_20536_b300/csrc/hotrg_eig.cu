@@ -1134,14 +1134,16 @@ __global__ void __launch_bounds__(SORT_THREADS) select_kernel(int dprime, double
     const int n_above = s_bounds[0], n_end = s_bounds[1];
     const int need = dprime - n_above;
     const int ncl = n_end - n_above;
-    // a block whose smallest listed eigenvalue reaches the cut listed too few
+    // a block whose smallest listed eigenvalue reaches the cut listed too few -- unless the
+    // cut itself lies within the cluster width of zero: then the cluster is the noise floor of
+    // the spectrum and which of its near-null states fill it does not matter
     for (int s = threadIdx.x; s < nsec; s += blockDim.x) {
         const int m = w.sec_start[s + 1] - w.sec_start[s];
         const int b = w.sec_b[s];
         if (b < m) {
             double lo = 1e300;
             for (int j = 0; j < b; ++j) lo = fmin(lo, lam[w.sec_cstart[s] + j]);
-            if (lo >= lcut - tol) atomicExch(w.status, (int)HOTRG_ENOCONV);
+            if (lo >= lcut - tol && lcut > tol) atomicExch(w.status, (int)HOTRG_ENOCONV);
         }
     }
     // sort the cluster by the tie rule in a separate power-of-two window
