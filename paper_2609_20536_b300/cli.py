@@ -72,9 +72,18 @@ def main(argv=None):
                           "ln_c": [res.step[k].ln_c for k in range(a.steps)],
                           "side": [res.step[k].side for k in range(a.steps)]}))
     elif a.cmd == "grid":
+        import os
+        from . import replicas
         from .workloads import grid_points
         allp = grid_points()
-        sel = [allp[(i * a.stride) % len(allp)] for i in range(a.n)]
+        everything = [allp[(i * a.stride) % len(allp)] for i in range(a.n)]
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        if world > 1:  # replicas: each rank runs its longest-first share, scalars gathered on the host
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        mine = replicas.shard(everything, world, rank)
+        sel = [everything[i] for i in mine]
         bs = a.block_sparse if prec != H.FP64 else 0
         plist = [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec, block_sparse=bs) for p in sel]
         tuned = None
@@ -89,8 +98,17 @@ def main(argv=None):
         counts = {}
         for p in sel:
             counts[p.d_cut] = counts.get(p.d_cut, 0) + 1
-        print(json.dumps({"points": a.n, "seconds": dt, "points_per_s": a.n / dt, "d_cut_counts": counts,
-                          "autotune": tuned, "status": sorted(set(r.status for r in res))}))
+        merged = replicas.gather({i: (r.lnz_per_site, r.status) for i, r in zip(mine, res)})
+        if world > 1:
+            import torch.distributed as dist
+            t = [None] * world
+            dist.all_gather_object(t, dt)
+            dt = max(t)
+            dist.destroy_process_group()
+        if rank == 0:
+            print(json.dumps({"points": len(merged), "ranks": world, "seconds": dt,
+                              "points_per_s": len(merged) / dt, "d_cut_counts_rank0": counts, "autotune": tuned,
+                              "status": sorted(set(v[1] for v in merged.values()))}))
     elif a.cmd == "surrogate":
         import numpy as np
         out = {}
