@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--points", type=int, default=2, help="points per bench step per GPU")
     ap.add_argument("--nstreams", type=int, default=0,
-                    help="worker streams of the batch runner (0: autotuned over 1..3 before the warm-up; "
+                    help="worker streams of the batch runner (0: autotuned over 1..min(3, points) before the warm-up; "
                          "1: points one after another on one stream)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
@@ -243,8 +243,9 @@ def main():
 
     tuned = None
     if args.nstreams == 0:
-        # autotune the worker-stream count on one bench step's worth of points (untimed)
-        best, secs = ctx.autotune_batch(batch(0), max_streams=3)
+        # autotune the worker-stream count on one bench step's worth of points (untimed); more
+        # streams than points per step would only idle
+        best, secs = ctx.autotune_batch(batch(0), max_streams=max(1, min(3, P)))
         tuned = {"chosen": best, "seconds_per_count": secs, "points": P}
         args.nstreams = best
 

@@ -72,8 +72,12 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sy
     for (int v = lane; v < BS_V; v += 32) counts[chunk * BS_V + v] = tab[w][v];
 }
 
-// One block of BS_V threads: per-value totals and bases, per-chunk starts, the group table.
-__global__ void __launch_bounds__(BS_V) bs_scan_kernel(const int32_t* __restrict__ cM, int64_t nM,
+// One block of 1024 threads (32 warps): per-value totals and bases, per-chunk
+// starts (a warp per value: strided sums, then a warp-wide exclusive scan over
+// the chunks, 32 at a time), the group table.
+constexpr int BS_SCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t* __restrict__ cM, int64_t nM,
                                                        const int32_t* __restrict__ cK, int64_t nK,
                                                        const int32_t* __restrict__ cN, int64_t nN,
                                                        int32_t* __restrict__ sM, int32_t* __restrict__ sK,
@@ -81,15 +85,18 @@ __global__ void __launch_bounds__(BS_V) bs_scan_kernel(const int32_t* __restrict
                                                        BsHeader* __restrict__ hdr, double* flops_acc, int kp_cap,
                                                        int32_t* status) {
     __shared__ int64_t tot[3][BS_V], base[3][BS_V];
-    const int v = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int v = threadIdx.x;  // thread 0 below builds the group table
     const int32_t* cs[3] = {cM, cK, cN};
     int32_t* ss[3] = {sM, sK, sN};
     const int64_t ns[3] = {nM, nK, nN};
-    for (int s = 0; s < 3; ++s) {
-        int64_t t = 0;
-        for (int64_t c = 0; c < ns[s]; ++c) t += cs[s][c * BS_V + v];
-        tot[s][v] = t;
-    }
+    for (int s = 0; s < 3; ++s)
+        for (int u = warp; u < BS_V; u += nw) {
+            int64_t t = 0;
+            for (int64_t c = lane; c < ns[s]; c += 32) t += cs[s][c * BS_V + u];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) tot[s][u] = t;
+        }
     __syncthreads();
     if (v == 0)
         for (int s = 0; s < 3; ++s) {
@@ -100,13 +107,21 @@ __global__ void __launch_bounds__(BS_V) bs_scan_kernel(const int32_t* __restrict
             }
         }
     __syncthreads();
-    for (int s = 0; s < 3; ++s) {
-        int64_t run = base[s][v];
-        for (int64_t c = 0; c < ns[s]; ++c) {
-            ss[s][c * BS_V + v] = (int32_t)run;
-            run += cs[s][c * BS_V + v];
+    for (int s = 0; s < 3; ++s)
+        for (int u = warp; u < BS_V; u += nw) {
+            int64_t run = base[s][u];
+            for (int64_t c0 = 0; c0 < ns[s]; c0 += 32) {
+                const int64_t c = c0 + lane;
+                const int32_t x = c < ns[s] ? cs[s][c * BS_V + u] : 0;
+                int32_t inc = x;  // inclusive scan over the 32 chunks
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                if (c < ns[s]) ss[s][c * BS_V + u] = (int32_t)(run + inc - x);
+                run += __shfl_sync(0xffffffffu, inc, 31);
+            }
         }
-    }
     if (v == 0) {
         int G = 0;
         int64_t mpad = 0, npad = 0, tiles = 0;
@@ -218,7 +233,7 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
     // slice pitch: the whole K set for small sets and Z2 (two blocks); half of it for larger U(1)
     // sets, whose blocks hold a small fraction of K (the device checks every block against it)
     out.kp_cap = bs_pitch(K.size, sym);
-    bs_scan_kernel<<<1, BS_V, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
+    bs_scan_kernel<<<1, BS_SCAN_THREADS, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
                                       starts[2], out.groups, out.hdr, facc, out.kp_cap, st);
     for (int i = 0; i < 3; ++i) {
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
