@@ -1,5 +1,8 @@
 """Initial tensors of the q = 2 generalized XY model (and the 2D Ising pin).
 
+The order q of the second coupling is a parameter (default 2, the thesis's
+model); only the coefficients a_n depend on it.
+
 TEST INFRASTRUCTURE (oracle).  Follows §3.2-§3.4 of the thesis:
 
 * Fourier / character coefficients (§3.2, Eq. 3.4):
@@ -43,15 +46,20 @@ M_RANGE = 50  # the thesis's truncation m in [-50, 50] (§3.2)
 PURE, IMP_M, IMP_M1 = "pure", "imp_m", "imp_m1"
 
 
-def fourier_coefficients(beta: float, delta: float, n_max: int, m_range: int = M_RANGE):
-    """a_n for n = -n_max..n_max (index n + n_max), §3.2 Eq. 3.4."""
+def fourier_coefficients(beta: float, delta: float, n_max: int, m_range: int = M_RANGE, q: int = 2):
+    """a_n for n = -n_max..n_max (index n + n_max), §3.2 Eq. 3.4.
+
+    q is the order of the second coupling, cos(q x): the thesis's model is
+    q = 2; the q >= 3 generalisations it names as future work (§4, §6) change
+    only these coefficients, a_n = sum_m I_{n - q m}(beta Delta) I_m(beta (1 - Delta)).
+    """
     x1 = beta * delta
     x2 = beta * (1.0 - delta)
     out = np.zeros(2 * n_max + 1)
     for n in range(-n_max, n_max + 1):
         s = 0.0
         for m in range(-m_range, m_range + 1):
-            s += bessel_i(n - 2 * m, x1) * bessel_i(m, x2)
+            s += bessel_i(n - q * m, x1) * bessel_i(m, x2)
         out[n + n_max] = s
     return out
 
@@ -94,9 +102,9 @@ def leg_charges(n_max: int, sym: str):
 
 
 def site_tensor(beta: float, delta: float, n_max: int, h: float = 0.0, h1: float = 0.0,
-                kind: str = PURE, m_range: int = M_RANGE):
-    """T[l,r,u,d] of shape (D0,)*4, FP64 (Eq. 3.6 / 3.15 / 3.20 / 3.21)."""
-    a = fourier_coefficients(beta, delta, n_max, m_range)
+                kind: str = PURE, m_range: int = M_RANGE, q: int = 2):
+    """T[l,r,u,d] of shape (D0,)*4, FP64 (Eq. 3.6 / 3.15 / 3.20 / 3.21); q as in fourier_coefficients."""
+    a = fourier_coefficients(beta, delta, n_max, m_range, q)
     D0 = 2 * n_max + 1
     n = np.arange(-n_max, n_max + 1)
     fcache = {}

@@ -236,12 +236,12 @@ def hotrg_run(T0, q0, n_steps, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL,
 
 
 def run_gxy(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, env_policy=0,
-            impurity=None, tie_rtol=TIE_RTOL) -> RunResult:
+            impurity=None, tie_rtol=TIE_RTOL, q=2) -> RunResult:
     """Convenience: build the gXY tensor (and an impurity) and run HOTRG."""
     sym = gxy.symmetry_of(h, h1)
-    T0 = gxy.site_tensor(beta, delta, n_max, h, h1, gxy.PURE)
+    T0 = gxy.site_tensor(beta, delta, n_max, h, h1, gxy.PURE, q=q)
     Ti = None
     if impurity is not None:
-        Ti = gxy.site_tensor(beta, delta, n_max, h, h1, impurity)
+        Ti = gxy.site_tensor(beta, delta, n_max, h, h1, impurity, q=q)
     q0 = gxy.leg_charges(n_max, sym)
     return hotrg_run(T0, q0, n_steps, d_cut, sym, env_policy, tie_rtol, Ti)
