@@ -97,7 +97,10 @@ typedef struct {
                              of §2.3.1); split forms only, and only pure runs: with an impurity tensor
                              or h != 0 it has no effect.  The result equals the dense form's up to the
                              split form's rounding. */
-    int32_t reserved;    /* must be 0 */
+    int32_t gxy_q;       /* order q of the second coupling (1 - Delta) cos(q theta): 0 or 2 = the
+                            thesis's q = 2 model; 1, 3, 4 the generalisations it names as future
+                            work, a_n = sum_m I_{n - q m}(beta Delta) I_m(beta (1 - Delta)).  The
+                            tensor, its charge rule and every kernel are otherwise the same. */
 } hotrg_params;
 
 /* Per-step scalars (device- or host-resident, see each entry point). */

@@ -167,8 +167,9 @@ static hotrg_status check_params(hotrg_ctx* ctx, const hotrg_params* p) {
     if (p->env_policy < 0 || p->env_policy > 1) return set_err(ctx, HOTRG_EINVAL, "env_policy must be 0 or 1");
     if (p->prec != HOTRG_FP64 && !ctx->tc_ok)
         return set_err(ctx, HOTRG_ENOTSUP, "tensor-core forms need an sm_103 device");
-    if (p->block_sparse < 0 || p->block_sparse > 1 || p->reserved != 0)
-        return set_err(ctx, HOTRG_EINVAL, "block_sparse must be 0 or 1 and reserved 0");
+    if (p->block_sparse < 0 || p->block_sparse > 1)
+        return set_err(ctx, HOTRG_EINVAL, "block_sparse must be 0 or 1");
+    if (p->gxy_q < 0 || p->gxy_q > 4) return set_err(ctx, HOTRG_EINVAL, "gxy_q must lie in [0, 4] (0: q = 2)");
     if (p->block_sparse && p->prec == HOTRG_FP64)
         return set_err(ctx, HOTRG_EINVAL, "block_sparse needs a split precision form");
     return HOTRG_OK;
@@ -739,7 +740,7 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
 // Batched points: LPT over worker streams, one CUDA graph per point class.
 // ---------------------------------------------------------------------------
 struct ClassKey {
-    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z, block_sparse;
+    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z, block_sparse, q;
     double tie_rtol, eig_tol;
     bool operator==(const ClassKey& o) const { return memcmp(this, &o, sizeof(ClassKey)) == 0; }
 };
@@ -759,6 +760,7 @@ static ClassKey class_of(const hotrg_params* p, int imp_kind) {
     k.hz = p->h == 0.0;
     k.h1z = p->h1 == 0.0;
     k.block_sparse = p->block_sparse;
+    k.q = p->gxy_q == 0 ? 2 : p->gxy_q;
     k.tie_rtol = p->tie_rtol;
     k.eig_tol = p->eig_tol;
     return k;

@@ -2,6 +2,8 @@
 // permutations, the FP64 reference-form GEMM, norms and traces.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace hotrg {
@@ -36,13 +38,13 @@ __device__ double bessel_in(int n, double x) {
     return sign * sum;
 }
 
-// a_n(beta, Delta) = sum_{m=-M..M} I_{n-2m}(beta Delta) I_m(beta (1 - Delta))   (Eq. 3.4)
+// a_n(beta, Delta) = sum_{m=-M..M} I_{n-qm}(beta Delta) I_m(beta (1 - Delta))   (Eq. 3.4; q = 2 in the thesis)
 // F(Q) for the pure tensor (Eq. 3.15) and the impurities (Eq. 3.20, 3.21).
 // One block: first every I_k needed (k = 0 .. kmax for the four arguments
 // beta Delta, beta (1 - Delta), beta h, beta h1) is tabulated in shared memory,
 // one thread per value; then one thread per coefficient sums the table in the
 // order of the formulas above.  All arguments are >= 0 and I_{-k} = I_k.
-__global__ void coeff_kernel(const hotrg_params* __restrict__ dp, int n_max, int m_range, int kind, int kmax,
+__global__ void coeff_kernel(const hotrg_params* __restrict__ dp, int n_max, int m_range, int kind, int q, int kmax,
                              double* a, double* F) {
     extern __shared__ double tab[];  // [4][kmax + 1]
     const double beta = dp->beta, delta = dp->delta, h = dp->h, h1 = dp->h1;
@@ -61,7 +63,7 @@ __global__ void coeff_kernel(const hotrg_params* __restrict__ dp, int n_max, int
         if (t < na) {
             const int n = t - n_max;
             double s = 0.0;
-            for (int m = -m_range; m <= m_range; ++m) s += at(I1, n - 2 * m) * at(I2, m);
+            for (int m = -m_range; m <= m_range; ++m) s += at(I1, n - q * m) * at(I2, m);
             a[t] = s;
         } else {
             const int Q = (t - na) - 4 * n_max;
@@ -128,9 +130,11 @@ void launch_init_tensor(const hotrg_params* p, const hotrg_params* dp, int kind,
     int sym = SYM_U1;
     if (p->h != 0.0) sym = SYM_NONE;
     else if (p->h1 != 0.0) sym = SYM_Z2;
-    // largest |order|: n_max + 2 m_range for a_n, 4 n_max + 2 m_range + 1 for F (<= 657 doubles a row)
-    const int kmax = 4 * n_max + 2 * m_range + 2;
-    coeff_kernel<<<1, 256, 4 * (kmax + 1) * sizeof(double), st>>>(dp, n_max, m_range, kind, kmax, a, F);
+    // largest |order|: n_max + q m_range for a_n, 4 n_max + 2 m_range + 1 for F (q <= 4: <= 865 doubles
+    // a row, 27.7 KB for the four tables)
+    const int q = p->gxy_q == 0 ? 2 : p->gxy_q;
+    const int kmax = std::max(n_max + q * m_range, 4 * n_max + 2 * m_range + 1) + 1;
+    coeff_kernel<<<1, 256, 4 * (kmax + 1) * sizeof(double), st>>>(dp, n_max, m_range, kind, q, kmax, a, F);
     const int total = na * na * na * na;
     gxy_tensor_kernel<<<(total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024, 256, 0, st>>>(
         a, F, n_max, sym, T, labels);

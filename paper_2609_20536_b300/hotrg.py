@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
         ("prec", ctypes.c_int32), ("env_policy", ctypes.c_int32), ("m_range", ctypes.c_int32),
         ("eig_max_sweeps", ctypes.c_int32), ("tkind", ctypes.c_int32),
         ("tie_rtol", ctypes.c_double), ("eig_tol", ctypes.c_double), ("side_rtol", ctypes.c_double),
-        ("block_sparse", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("block_sparse", ctypes.c_int32), ("gxy_q", ctypes.c_int32),
     ]
 
 
@@ -131,9 +131,9 @@ lib = _load()
 
 
 def params(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, prec=FP64, env_policy=0, m_range=50,
-           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0, side_rtol=0.0, block_sparse=0):
+           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0, side_rtol=0.0, block_sparse=0, q=2):
     return Params(beta, delta, h, h1, n_max, d_cut, n_steps, prec, env_policy, m_range,
-                  eig_max_sweeps, tkind, tie_rtol, eig_tol, side_rtol, block_sparse, 0)
+                  eig_max_sweeps, tkind, tie_rtol, eig_tol, side_rtol, block_sparse, q)
 
 
 def hotrg_create(workspace_bytes=0, stream=0):

@@ -37,3 +37,6 @@ BATCH_ORACLE = BATCH[:3]
 # noise moves the oracle's own ln Z / N by ~1e-7 at 14 steps (and 1e-10 noise,
 # the split form's level, by ~1e-8 already at 10 steps; D_cut = 13 is benign).
 ILL_CONDITIONED = (1.0, 0.5, 2, 12, 14)
+
+# The q != 2 couplings (cos(q theta)), (beta, Delta, n_max, D_cut, n_steps, q).
+Q_SHAPES = [(1.1, 0.5, 3, 16, 12, 3), (0.9, 0.7, 3, 13, 10, 4), (1.2, 0.4, 2, 12, 10, 1)]

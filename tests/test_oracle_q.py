@@ -54,3 +54,17 @@ def test_q3_two_by_two_lattice_three_routes():
     assert abs(brute - direct) < 1e-13 and abs(hot - brute) < 1e-13
     # and it differs from the q = 2 model
     assert abs(hot - OH.run_gxy(beta, delta, nm, 10 ** 3, 2).lnz_per_site) > 1e-3
+
+
+@pytest.mark.parametrize("point", __import__("parity_points").Q_SHAPES)
+def test_q_parity_points_are_well_conditioned(point):
+    # as for the q = 2 points: rounding-level input noise (1e-15 for the FP64
+    # form, 1e-10 for the split form) must move ln Z/N far below the tolerance
+    beta, delta, nm, dcut, steps, q = point
+    T0 = gxy.site_tensor(beta, delta, nm, q=q)
+    q0 = gxy.leg_charges(nm, "u1")
+    ref = OH.hotrg_run(T0, q0, steps, dcut, "u1").lnz_per_site
+    for eta, bound in ((1e-15, 2e-12), (1e-10, 2e-10)):
+        rng = np.random.default_rng(3)
+        Tp = T0 * (1.0 + eta * rng.standard_normal(T0.shape))
+        assert abs(OH.hotrg_run(Tp, q0, steps, dcut, "u1").lnz_per_site - ref) <= bound
