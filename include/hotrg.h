@@ -57,7 +57,7 @@ typedef enum {
     HOTRG_EINVAL = -1,   /* invalid argument (sizes, parameters, null pointer) */
     HOTRG_ENOMEM = -2,   /* device or host allocation failed */
     HOTRG_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
-    HOTRG_ENOCONV = -4,  /* eigensolver did not converge within its sweep cap */
+    HOTRG_ENOCONV = -4,  /* eigensolver (sweep cap) or zero-field fit did not converge */
     HOTRG_ETIMEOUT = -5, /* a bounded device wait ran out */
     HOTRG_ENOTSUP = -6   /* form not available in this build / on this device */
 } hotrg_status;
@@ -350,6 +350,88 @@ hotrg_status hotrg_surrogate_refine(hotrg_ctx* ctx, hotrg_mlp* m, const hotrg_sc
                                     const hotrg_params* base, const double* X, int32_t n, double threshold,
                                     double hb, double hbar, double dh, int32_t nstreams, double* y,
                                     double* spread, int32_t* solved, int32_t* n_solved);
+
+/* Phase-boundary extraction (§3.4 results, Table 3.1).
+ *
+ * The thesis locates the transitions from temperature scans at fixed Delta:
+ * the peaks of C_V(T) at zero field, and the peak of chi(T) (Eq. 3.18) at a
+ * small central field hbar, extrapolated to hbar -> 0.  The extrapolation is
+ * read as the least-squares fit T_p(hbar) = a + b hbar^c: the thesis prints
+ * a, b, c for Delta = 0.32 (a being the zero-field T_c of Table 3.1 there)
+ * and cites the form without printing it.
+ *
+ * hotrg_find_peaks and hotrg_fit_tc are host only (no context, no device
+ * work); hotrg_phase_scan runs its HOTRG points through hotrg_run_batch. */
+
+/* Peaks of y sampled on a strictly ascending grid x (n host points).  A
+ * peak is an interior local maximum: a run y[i] = ... = y[j] (1 <= i <= j <=
+ * n - 2) with y[i-1] < y[i] and y[j] > y[j+1], taken at k = (i + j) / 2
+ * (integer division).  Its prominence is y[k] minus the higher of the two
+ * smallest values met walking left and right from k up to the first
+ * strictly higher value or the end.  Peaks with prominence >= min_prominence
+ * count and *n_found receives their number; of these the cap most prominent
+ * (ties: smaller k) are written in ascending x: x_peak / y_peak the vertex
+ * of the parabola through the samples k-1, k, k+1 (the sample k itself when
+ * the three values are equal), prominence (may be NULL) the prominences.
+ * Errors: HOTRG_EINVAL (NULL x, y or n_found; NULL x_peak / y_peak with
+ * cap > 0; n < 0; cap < 0; x not strictly ascending; a non-finite x, y or
+ * min_prominence). */
+hotrg_status hotrg_find_peaks(const double* x, const double* y, int32_t n, double min_prominence, int32_t cap,
+                              double* x_peak, double* y_peak, double* prominence, int32_t* n_found);
+
+typedef struct {
+    double a, b, c;             /* T_p(hbar) = a + b hbar^c; a = T_c in the limit hbar -> 0 */
+    double a_err, b_err, c_err; /* sqrt(diag(s^2 (J^T J)^-1)), s^2 = rss / (n - 3), J = d model / d(a, b, c);
+                                   0 when n = 3 */
+    double rss;                 /* residual sum of squares at (a, b, c) */
+    int32_t n;                  /* points fitted (0: no fit was made) */
+    int32_t at_bound;           /* 1 when c sits on c_lo or c_hi (always when c_lo = c_hi) */
+} hotrg_tc_fit;
+
+/* Least-squares fit of T_p(hbar) = a + b hbar^c over n host points, with
+ * c in [c_lo, c_hi] (c_lo = c_hi fixes c; c_lo <= 0 and c_hi <= 0 together
+ * select the bracket [0.05, 2]).  For each c the best (a, b) is linear; the
+ * profile residual is scanned on 2001 evenly spaced c and its stationary
+ * point around the best one solved to full precision; a minimum on a bound
+ * stays on it.  Errors: HOTRG_EINVAL (NULL pointers; fewer than 3 distinct
+ * hbar; hbar <= 0; a non-finite value; 0 < c_lo <= c_hi violated),
+ * HOTRG_ENOCONV (no stationary point found in the bracket). */
+hotrg_status hotrg_fit_tc(const double* hbar, const double* t_peak, int32_t n, double c_lo, double c_hi,
+                          hotrg_tc_fit* out);
+
+typedef struct {
+    int32_t field;         /* HOTRG_T_IMP_M: chi = dm/dh in the field h; HOTRG_T_IMP_M1: chi1 = dm1/dh1 in h1;
+                              0: the thesis's choice, h for Delta > 0.36 and h1 for Delta <= 0.36 */
+    int32_t nstreams;      /* worker streams of hotrg_run_batch, 0..16 (0: the tuned count) */
+    double dh;             /* field step of chi's central difference, > 0 and <= every hbar */
+    double hb;             /* beta step of C_V's central difference, > 0 */
+    double min_prominence; /* of a chi peak (hotrg_find_peaks), finite */
+    double c_lo, c_hi;     /* exponent bracket of the fit (hotrg_fit_tc) */
+} hotrg_phase_opts;
+
+/* Temperature scans at one Delta.  base fixes the gXY model and the run
+ * (delta, n_max, d_cut, n_steps, prec, block_sparse, ...; tkind must be
+ * HOTRG_T_PURE); its beta, h and h1 are ignored.  temps: n_t >= 3 strictly
+ * ascending positive temperatures (host), beta_j = 1 / temps[j].
+ *   chi[k * n_t + j] = [m(hbar[k] + dh) - m(hbar[k] - dh)] / (2 dh) at beta_j,
+ *     m the impurity ratio of the selected field (the other field 0): the
+ *     runs and arithmetic of hotrg_observables' chi / chi1 at hbar = hbar[k],
+ *     so the values equal its bit for bit (n_h >= 0 rows);
+ *   cv[j] (cv may be NULL: no pure runs) = beta_j^2 [lnZ(beta_j + hb)
+ *     - 2 lnZ(beta_j) + lnZ(beta_j - hb)] / hb^2 at h = h1 = 0, hotrg_obs.cv
+ *     bit for bit;
+ *   t_peak[k] (may be NULL) = x_peak of the most prominent peak of row k
+ *     (hotrg_find_peaks with opts->min_prominence), NaN when the row has none;
+ *   *fit (may be NULL) = hotrg_fit_tc over the rows with a peak, or n = 0 and
+ *     NaN parameters when fewer than three rows have one;
+ *   *field_used (may be NULL) = the field applied (HOTRG_T_IMP_M or _M1).
+ * 2 n_h n_t impurity runs and 3 n_t pure runs go through hotrg_run_batch.
+ * Synchronous; host outputs.  Errors: HOTRG_EINVAL (arguments); a run's
+ * status (the tables are then undefined); HOTRG_ENOCONV from the fit (the
+ * tables and t_peak are valid). */
+hotrg_status hotrg_phase_scan(hotrg_ctx* ctx, const hotrg_params* base, const double* temps, int32_t n_t,
+                              const double* hbar, int32_t n_h, const hotrg_phase_opts* opts, double* cv,
+                              double* chi, double* t_peak, hotrg_tc_fit* fit, int32_t* field_used);
 
 /* Per-kernel-class timing recorded with CUDA events on the context's stream
  * (the stream every library kernel runs on).  Classes of the contraction

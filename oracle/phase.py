@@ -84,8 +84,11 @@ def vertex(x3, y3):
 
     The parabola y = A u^2 + B u + C in u = x - x3[1] interpolates the three
     points (the 3 x 3 Vandermonde system); x_v = x3[1] - B / (2 A),
-    y_v = C - B^2 / (4 A).  Needs A != 0.
+    y_v = C - B^2 / (4 A).  Three equal values (the inside of a plateau of
+    three or more samples) have no vertex: the middle sample is returned.
     """
+    if y3[0] == y3[1] == y3[2]:
+        return float(x3[1]), float(y3[1])
     u = np.asarray(x3, dtype=np.float64) - float(x3[1])
     V = np.stack([u * u, u, np.ones(3)], axis=1)
     A, B, C = np.linalg.solve(V, np.asarray(y3, dtype=np.float64))

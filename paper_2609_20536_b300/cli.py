@@ -4,12 +4,16 @@
   python -m paper_2609_20536_b300.cli contract --M 65536 --N 4096 --K 4096 [--prec split] [--repeat 1]
   python -m paper_2609_20536_b300.cli grid --n 64 [--nstreams 0]
   python -m paper_2609_20536_b300.cli surrogate [--nb 12 --nd 8 --d-cut 12 --steps 16]
+  python -m paper_2609_20536_b300.cli phase --delta 0.32 [--t-lo 0.5 --t-hi 1.2 --n-t 36 --hbar 0.005,0.01,0.02,0.04]
 
 `run` prints ln Z/N and the per-step scalars of one point; `grid` times a
 sample of the 64 x 64 (beta, Delta) grid with D_cut drawn from {24, 32, 48,
 64} through the batch runner; `surrogate` builds a training grid of
 observables, trains the MLP ensemble, audits it against HOTRG on random
-points and refines near the C_V / chi maxima; `contract` times one C = A B^T of the given
+points and refines near the C_V / chi maxima; `phase` scans one Delta in
+temperature and prints the C_V peaks, the chi peak at each central field and
+the zero-field T_c of the fit T_p = a + b hbar^c (a row of Table 3.1 at this
+bond dimension); `contract` times one C = A B^T of the given
 shape through the contraction engine (random FP64 operands generated on the
 device).
 """
@@ -49,6 +53,19 @@ def main(argv=None):
     sg.add_argument("--threshold", type=float, default=1e-3)
     sg.add_argument("--audit", type=int, default=64)
     sg.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
+    ph = sub.add_parser("phase")
+    ph.add_argument("--delta", type=float, required=True)
+    ph.add_argument("--t-lo", type=float, default=0.5)
+    ph.add_argument("--t-hi", type=float, default=1.2)
+    ph.add_argument("--n-t", type=int, default=36)
+    ph.add_argument("--hbar", default="0.005,0.01,0.02,0.04", help="central fields of chi, comma separated")
+    ph.add_argument("--field", default="auto", choices=["auto", "h", "h1"])
+    ph.add_argument("--dh", type=float, default=1e-3)
+    ph.add_argument("--n-max", type=int, default=4)
+    ph.add_argument("--d-cut", type=int, default=24)
+    ph.add_argument("--steps", type=int, default=30)
+    ph.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
+    ph.add_argument("--nstreams", type=int, default=0)
     c = sub.add_parser("contract")
     c.add_argument("--M", type=int, required=True)
     c.add_argument("--N", type=int, required=True)
@@ -145,6 +162,31 @@ def main(argv=None):
         out["peak_beta_cv_chi"] = pk.tolist()
         sur.close()
         print(json.dumps(out))
+    elif a.cmd == "phase":
+        import numpy as np
+        temps = np.linspace(a.t_lo, a.t_hi, a.n_t)
+        hbars = [float(v) for v in a.hbar.split(",") if v]
+        field = {"auto": 0, "h": H.T_IMP_M, "h1": H.T_IMP_M1}[a.field]
+        base = H.params(1.0, a.delta, a.n_max, a.d_cut, a.steps, prec=prec,
+                        block_sparse=1 if prec != H.FP64 else 0)
+        t0 = time.perf_counter()
+        res = ctx.phase_scan(base, temps, hbars, field=field, dh=a.dh, nstreams=a.nstreams, check=False)
+        dt = time.perf_counter() - t0
+        if res["status"] not in (H.OK, H.ENOCONV):
+            print(json.dumps({"status": res["status"], "error": H.hotrg_last_error(ctx.handle)}))
+            ctx.close()
+            return 1
+        cv_peaks, _ = H.hotrg_find_peaks(temps, res["cv"], 0.0, 2)
+        f = res["fit"]
+        print(json.dumps({"delta": a.delta, "field": {H.T_IMP_M: "h", H.T_IMP_M1: "h1"}[res["field"]],
+                          "d_cut": a.d_cut, "seconds": dt,
+                          "T_cv_peaks": [x for x, _, _ in cv_peaks],
+                          "hbar": hbars, "T_chi_peak": [None if np.isnan(v) else v for v in res["t_peak"]],
+                          "T_c_zero_field": None if f.n == 0 else f.a,
+                          "fit": None if f.n == 0 else {"a": f.a, "b": f.b, "c": f.c, "a_err": f.a_err,
+                                                         "b_err": f.b_err, "c_err": f.c_err,
+                                                         "at_bound": f.at_bound},
+                          "status": res["status"]}))
     else:
         g = torch.Generator(device="cuda").manual_seed(0)
         A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)

@@ -71,6 +71,22 @@ class Obs(ctypes.Structure):
     ]
 
 
+class TcFit(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double),
+        ("a_err", ctypes.c_double), ("b_err", ctypes.c_double), ("c_err", ctypes.c_double),
+        ("rss", ctypes.c_double), ("n", ctypes.c_int32), ("at_bound", ctypes.c_int32),
+    ]
+
+
+class PhaseOpts(ctypes.Structure):
+    _fields_ = [
+        ("field", ctypes.c_int32), ("nstreams", ctypes.c_int32), ("dh", ctypes.c_double),
+        ("hb", ctypes.c_double), ("min_prominence", ctypes.c_double), ("c_lo", ctypes.c_double),
+        ("c_hi", ctypes.c_double),
+    ]
+
+
 class Scaling(ctypes.Structure):
     _fields_ = [
         ("x_mean", ctypes.c_double * 2), ("x_std", ctypes.c_double * 2),
@@ -120,6 +136,13 @@ def _load():
     lib.hotrg_contract.argtypes = [vp, i32, i32, i32, i32, vp, ctypes.c_int64, vp, ctypes.c_int64, vp,
                                    ctypes.c_int64]
     lib.hotrg_contract.restype = ctypes.c_int
+    lib.hotrg_find_peaks.argtypes = [dp, dp, i32, f64, i32, dp, dp, dp, ip]
+    lib.hotrg_find_peaks.restype = ctypes.c_int
+    lib.hotrg_fit_tc.argtypes = [dp, dp, i32, f64, f64, ctypes.POINTER(TcFit)]
+    lib.hotrg_fit_tc.restype = ctypes.c_int
+    lib.hotrg_phase_scan.argtypes = [vp, ctypes.POINTER(Params), dp, i32, dp, i32, ctypes.POINTER(PhaseOpts), dp,
+                                     dp, dp, ctypes.POINTER(TcFit), ip]
+    lib.hotrg_phase_scan.restype = ctypes.c_int
     lib.hotrg_profile_enable.argtypes = [vp, i32]
     lib.hotrg_profile_enable.restype = ctypes.c_int
     lib.hotrg_profile_read.argtypes = [vp, ctypes.POINTER(Profile)]
@@ -243,6 +266,62 @@ def hotrg_scaling_fit(X, Y):
     if st != OK:
         raise HotrgError(st, "hotrg_scaling_fit")
     return s
+
+
+def hotrg_find_peaks(x, y, min_prominence=0.0, cap=8):
+    """Peaks of y(x) (host C++): ([(x_v, y_v, prominence), ...] in ascending x, number found)."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if x.shape != y.shape or x.ndim != 1:
+        raise ValueError("x and y must be 1-D arrays of one length")
+    xp, yp, pr = (ctypes.c_double * max(cap, 1))(), (ctypes.c_double * max(cap, 1))(), (ctypes.c_double * max(cap, 1))()
+    nf = ctypes.c_int32(0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = lib.hotrg_find_peaks(x.ctypes.data_as(dp), y.ctypes.data_as(dp), len(x), min_prominence, cap, xp, yp, pr,
+                              ctypes.byref(nf))
+    if st != OK:
+        raise HotrgError(st, "hotrg_find_peaks")
+    return [(xp[i], yp[i], pr[i]) for i in range(min(cap, nf.value))], nf.value
+
+
+def hotrg_fit_tc(hbar, t_peak, c_lo=0.0, c_hi=0.0):
+    """Zero-field fit T_p(hbar) = a + b hbar^c (host C++); returns a TcFit."""
+    import numpy as np
+    h = np.ascontiguousarray(hbar, dtype=np.float64)
+    t = np.ascontiguousarray(t_peak, dtype=np.float64)
+    if h.shape != t.shape or h.ndim != 1:
+        raise ValueError("hbar and t_peak must be 1-D arrays of one length")
+    out = TcFit()
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = lib.hotrg_fit_tc(h.ctypes.data_as(dp), t.ctypes.data_as(dp), len(h), c_lo, c_hi, ctypes.byref(out))
+    if st != OK:
+        raise HotrgError(st, "hotrg_fit_tc")
+    return out
+
+
+def hotrg_phase_scan(ctx, base, temps, hbars, field=0, dh=1e-3, hb=1e-3, min_prominence=0.0, nstreams=0,
+                     c_lo=0.0, c_hi=0.0, with_cv=True, check=True):
+    """Temperature scans at one Delta: dict with cv (n_t or None), chi (n_h x n_t), t_peak (n_h), fit, field."""
+    import numpy as np
+    temps = np.ascontiguousarray(temps, dtype=np.float64)
+    hbars = np.ascontiguousarray(hbars, dtype=np.float64)
+    nt, nh = len(temps), len(hbars)
+    cv = np.zeros(nt) if with_cv else None
+    chi = np.zeros((nh, nt))
+    tp = np.zeros(nh)
+    fit = TcFit()
+    used = ctypes.c_int32(0)
+    opts = PhaseOpts(field, nstreams, dh, hb, min_prominence, c_lo, c_hi)
+    dp = ctypes.POINTER(ctypes.c_double)
+
+    def ptr(a):
+        return a.ctypes.data_as(dp) if a is not None and a.size else None
+    st = lib.hotrg_phase_scan(ctx, ctypes.byref(base), ptr(temps), nt, ptr(hbars), nh, ctypes.byref(opts),
+                              ptr(cv) if with_cv else None, ptr(chi), ptr(tp), ctypes.byref(fit), ctypes.byref(used))
+    if check:
+        _check(ctx, st)
+    return {"cv": cv, "chi": chi, "t_peak": tp, "fit": fit, "field": used.value, "status": st}
 
 
 def hotrg_contract(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc):
@@ -462,3 +541,6 @@ class Context:
 
     def observables_batch(self, plist, hb=1e-3, hbar=0.01, dh=1e-3, nstreams=2):
         return hotrg_observables_batch(self.handle, plist, hb, hbar, dh, nstreams)
+
+    def phase_scan(self, base, temps, hbars, **kw):
+        return hotrg_phase_scan(self.handle, base, temps, hbars, **kw)

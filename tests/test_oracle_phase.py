@@ -38,6 +38,10 @@ def test_no_peak_cases():
     assert OP.local_maxima([2.0, 2.0, 2.0, 2.0]) == []  # flat
     assert OP.local_maxima([0.0, 1.0, 1.0, 1.0, 1.0, 0.0]) == [2]  # plateau: its middle (scipy's rule)
     assert OP.find_peaks([0.0, 1.0, 2.0], [3.0, 2.0, 1.0]) == []
+    # a plateau of four samples: the flat window's peak is its middle sample; of two: between them
+    assert OP.find_peaks([0.0, 1.0, 2.0, 3.0, 4.0, 5.0], [0.0, 1.0, 1.0, 1.0, 1.0, 0.0]) == [(2.0, 1.0, 1.0)]
+    (xv, yv, pr), = OP.find_peaks([0.0, 1.0, 2.0, 3.0], [0.0, 1.0, 1.0, 0.0])
+    assert abs(xv - 1.5) < 1e-15 and abs(yv - 1.125) < 1e-15 and pr == 1.0
 
 
 def test_vertex_is_exact_on_quadratics():
