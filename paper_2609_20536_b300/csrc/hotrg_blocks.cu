@@ -17,6 +17,8 @@
 // (operand and output for M and N, A and B for K).  Groups whose value has
 // no element of K still get tiles: their block of C is zero and is written.
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 
 #include "internal.cuh"
 
@@ -45,11 +47,69 @@ __device__ __forceinline__ int bs_value(const BsSet& S, int sym, int64_t idx64, 
 
 constexpr int BS_WARPS = 8;  // warps per block in the counting passes
 
+// Table centre of one product: value v goes to slot v - centre + BS_VOFF.
+// The centre stays 0 while every value the legs allow lies in
+// [-BS_VOFF, BS_V - BS_VOFF); otherwise it is the midpoint of that range.  In
+// the ordered phase the kept U(1) window can drift away from charge 0 (an
+// exact +-q pair split at the cut keeps +q, and the fused charge q_a + q_b
+// doubles an off-centre window every two steps) while its span stays small,
+// so a centred table still holds it.  One block: warp w takes leg w % 3 of
+// set w / 3 (its min and max label); thread 0 adds up the signed ranges.
+__global__ void __launch_bounds__(32 * 9) bs_centre_kernel(BsSet M, BsSet K, BsSet N, int sym,
+                                                            int32_t* __restrict__ centre) {
+    __shared__ int lmin[9], lmax[9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const BsSet& S = w < 3 ? M : (w < 6 ? K : N);
+    const int f = w % 3;
+    int lo = INT_MAX, hi = INT_MIN;
+    if (f < S.nf)
+        for (int64_t i = lane; i < S.f[f].ext; i += 32) {
+            const int q = S.f[f].lab[i];
+            lo = min(lo, q);
+            hi = max(hi, q);
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane == 0) {
+        lmin[w] = lo;
+        lmax[w] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (sym != SYM_U1) {
+        *centre = 0;
+        return;
+    }
+    int64_t vlo = INT64_MAX, vhi = INT64_MIN;
+    for (int s = 0; s < 3; ++s) {
+        const BsSet& T = s == 0 ? M : (s == 1 ? K : N);
+        int64_t a = 0, b = 0;
+        for (int g = 0; g < T.nf; ++g) {
+            const int64_t mn = lmin[s * 3 + g], mx = lmax[s * 3 + g];
+            if (mn > mx) continue;  // a leg without labels contributes nothing
+            a += T.f[g].sgn > 0 ? mn * T.f[g].sgn : mx * T.f[g].sgn;
+            b += T.f[g].sgn > 0 ? mx * T.f[g].sgn : mn * T.f[g].sgn;
+        }
+        vlo = a < vlo ? a : vlo;
+        vhi = b > vhi ? b : vhi;
+    }
+    if (vlo >= -BS_VOFF && vhi < BS_V - BS_VOFF) {
+        *centre = 0;
+    } else {
+        const int64_t c = vlo + (vhi - vlo) / 2;
+        *centre = (int32_t)(c > INT32_MAX / 2 ? INT32_MAX / 2 : (c < INT32_MIN / 2 ? INT32_MIN / 2 : c));
+    }
+}
+
 // counts[chunk][BS_V]: elements of each value in every BS_CHUNK-element chunk.
 __global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sym, int32_t* __restrict__ counts,
-                                                                 int64_t nchunks, int32_t* status) {
+                                                                 int64_t nchunks, const int32_t* __restrict__ centre,
+                                                                 int32_t* status) {
     __shared__ int32_t tab[BS_WARPS][BS_V];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int shift = BS_VOFF - *centre;
     const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
     for (int v = lane; v < BS_V; v += 32) tab[w][v] = 0;
     __syncwarp();
@@ -59,7 +119,7 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sy
         const int64_t idx = b + lane;
         const bool act = idx < hi;
         int64_t o0, o1;
-        const int v = act ? bs_value(S, sym, idx, o0, o1) + BS_VOFF : -1;
+        const int v = act ? bs_value(S, sym, idx, o0, o1) + shift : -1;
         // an element whose value falls outside the table is left out here and in the
         // placing pass alike (so every counted position is written) and fails the run
         const bool ok = act && v >= 0 && v < BS_V;
@@ -162,12 +222,14 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
 
 // Writes the two offsets of every element at its sorted position.
 __global__ void __launch_bounds__(32 * BS_WARPS) bs_place_kernel(BsSet S, int sym, const int32_t* __restrict__ starts,
-                                                                 int64_t nchunks, int64_t* __restrict__ off0,
+                                                                 int64_t nchunks, const int32_t* __restrict__ centre,
+                                                                 int64_t* __restrict__ off0,
                                                                  int64_t* __restrict__ off1) {
     __shared__ int32_t tab[BS_WARPS][BS_V];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
     if (chunk >= nchunks) return;
+    const int shift = BS_VOFF - *centre;
     for (int v = lane; v < BS_V; v += 32) tab[w][v] = starts[chunk * BS_V + v];
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
@@ -176,7 +238,7 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_place_kernel(BsSet S, int sy
         const int64_t idx = b + lane;
         const bool act = idx < hi;
         int64_t o0 = 0, o1 = 0;
-        int v = act ? bs_value(S, sym, idx, o0, o1) + BS_VOFF : -1;
+        int v = act ? bs_value(S, sym, idx, o0, o1) + shift : -1;
         const bool ok = act && v >= 0 && v < BS_V;
         const unsigned okm = __ballot_sync(0xffffffffu, ok);
         const unsigned m = __match_any_sync(0xffffffffu, ok ? v : -1) & okm;
@@ -200,7 +262,7 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN) {
         const int64_t ch = (n + BS_CHUNK - 1) / BS_CHUNK;
         b += 2 * a256(ch * BS_V * 4) + 2 * a256(n * 8);
     }
-    return b + a256(sizeof(BsGroup) * BS_V) + a256(sizeof(BsHeader));
+    return b + a256(sizeof(BsGroup) * BS_V) + a256(sizeof(BsHeader)) + 256;
 }
 
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
@@ -221,13 +283,15 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
     }
     out.groups = (BsGroup*)ws_alloc(ctx, sizeof(BsGroup) * BS_V);
     out.hdr = (BsHeader*)ws_alloc(ctx, sizeof(BsHeader));
-    if (!out.groups || !out.hdr) return set_err(ctx, HOTRG_ENOMEM, "block plan workspace exhausted");
+    int32_t* centre = (int32_t*)ws_alloc(ctx, 256);
+    if (!out.groups || !out.hdr || !centre) return set_err(ctx, HOTRG_ENOMEM, "block plan workspace exhausted");
     int32_t* st = umma_status_word(ctx);
     if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
     cudaStream_t s = ctx->stream;
+    bs_centre_kernel<<<1, 32 * 9, 0, s>>>(M, K, N, sym, centre);
     for (int i = 0; i < 3; ++i) {
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
-        bs_count_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, counts[i], nch[i], st);
+        bs_count_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, counts[i], nch[i], centre, st);
     }
     double* facc = (ctx->prof.on && ctx->prof.dflops) ? ctx->prof.dflops + prof_class : nullptr;
     // slice pitch: the whole K set for small sets and Z2 (two blocks); half of it for larger U(1)
@@ -237,9 +301,10 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
                                       starts[2], out.groups, out.hdr, facc, out.kp_cap, st);
     for (int i = 0; i < 3; ++i) {
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
-        bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], offs[i][0], offs[i][1]);
+        bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], centre, offs[i][0],
+                                                        offs[i][1]);
     }
-    HOTRG_COUNT(7);
+    HOTRG_COUNT(8);
     HOTRG_LAUNCH_CHECK(ctx, "block planner");
     out.offM0 = offs[0][0];
     out.offM1 = offs[0][1];

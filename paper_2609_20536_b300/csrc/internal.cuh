@@ -195,8 +195,9 @@ struct BsPlan {  // device pointers (workspace) plus the host-known set sizes
 };
 size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // Enqueues the planner for C = A B^T over index sets (M, K, N) with the given
-// symmetry; a label sum outside |v| < 64 records HOTRG_ENOTSUP in the engine's
-// status word.
+// symmetry; the value table (BS_V slots) is centred on the product's range of
+// label sums, and a product whose sums span BS_V or more values records
+// HOTRG_ENOTSUP in the engine's status word.
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
                      BsPlan& out);
 // Slice row pitch of a grouped product: the whole K set rounded to 32 for small sets and

@@ -40,3 +40,10 @@ ILL_CONDITIONED = (1.0, 0.5, 2, 12, 14)
 
 # The q != 2 couplings (cos(q theta)), (beta, Delta, n_max, D_cut, n_steps, q).
 Q_SHAPES = [(1.1, 0.5, 3, 16, 12, 3), (0.9, 0.7, 3, 13, 10, 4), (1.2, 0.4, 2, 12, 10, 1)]
+
+# Ordered phase (T = 0.55 at Delta = 0.32): the kept U(1) window drifts away
+# from charge 0 late in the run (an exact +-q pair split at the cut keeps +q,
+# and fusing doubles an off-centre window every two steps), so the signed
+# label sums of the block-sparse products leave [-64, 63] (by step 25 at
+# D_cut = 12, step 29 at D_cut = 24) while their span stays small.
+DRIFT_SHAPES = [(1 / 0.55, 0.32, 4, 12, 30), (1 / 0.55, 0.32, 4, 24, 30)]

@@ -12,7 +12,7 @@ import pytest
 from oracle import gxy
 from oracle import hotrg as OH
 
-from parity_points import BATCH, SPLIT_SHAPES
+from parity_points import BATCH, DRIFT_SHAPES, SPLIT_SHAPES
 
 pytestmark = pytest.mark.gpu
 
@@ -49,6 +49,18 @@ def test_block_sparse_lnz_against_oracle(H, C, beta, delta, nm, dcut, steps):
         if margin > 1e-9 and rs.eps_left > 1e-13:
             assert bs.step[k].side == rs.side
         assert abs(bs.step[k].ln_c - rs.ln_c) <= 1e-7 * max(1.0, abs(rs.ln_c))
+
+
+@pytest.mark.parametrize("beta,delta,nm,dcut,steps", DRIFT_SHAPES)
+def test_block_sparse_drifted_charge_window(H, C, beta, delta, nm, dcut, steps):
+    # the kept U(1) window has drifted far from charge 0: the planner's value table
+    # follows the products' label range instead of failing with HOTRG_ENOTSUP
+    ref = OH.run_gxy(beta, delta, nm, dcut, steps)
+    bs = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+    dense = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16)])[0]
+    assert bs.status == 0
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-9, bs.lnz_per_site - ref.lnz_per_site
+    assert abs(bs.lnz_per_site - dense.lnz_per_site) <= 2e-10
 
 
 def test_block_sparse_z2_field(H, C):

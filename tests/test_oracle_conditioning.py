@@ -13,7 +13,7 @@ import pytest
 from oracle import gxy
 from oracle import hotrg as OH
 
-from parity_points import BATCH_ORACLE, FP64_SHAPES, ILL_CONDITIONED, SPLIT_SHAPES
+from parity_points import BATCH_ORACLE, DRIFT_SHAPES, FP64_SHAPES, ILL_CONDITIONED, SPLIT_SHAPES
 
 
 def spread(point, eta, seeds=(1, 2)):
@@ -34,7 +34,7 @@ def test_fp64_points_are_well_conditioned(point):
     assert spread(point, 1e-15) <= 2e-12
 
 
-@pytest.mark.parametrize("point", SPLIT_SHAPES + BATCH_ORACLE)
+@pytest.mark.parametrize("point", SPLIT_SHAPES + BATCH_ORACLE + DRIFT_SHAPES)
 def test_split_points_are_well_conditioned(point):
     # the split form's per-step ln c_k are accurate to ~1e-10 relative
     assert spread(point, 1e-10) <= 2e-10
@@ -47,3 +47,26 @@ def test_ill_conditioned_counter_example():
     short = ILL_CONDITIONED[:4] + (10,)
     assert spread(short, 1e-15) <= 2e-12
     assert spread(short, 1e-10) > 1e-9
+
+
+def label_sum_bound(point):
+    """Largest |q_x| + |q_h| + |q_v| over the steps of the oracle's run: a bound on the
+    signed three-leg label sums of the block-sparse products (new bond, horizontal, vertical)."""
+    beta, delta, nm, dcut, steps = point
+    T = gxy.site_tensor(beta, delta, nm)
+    T = T / np.linalg.norm(T)
+    qh = np.asarray(gxy.leg_charges(nm, "u1"), dtype=np.int64)
+    qv = qh.copy()
+    worst = 0
+    for _ in range(steps):
+        qh0, qv0 = qh, qv
+        T, qh, qv, _, _ = OH.hotrg_step(T, qh, qv, dcut, "u1", 0, OH.TIE_RTOL, None)
+        worst = max(worst, int(np.abs(qv).max() + np.abs(qh0).max() + np.abs(qv0).max()))
+    return worst, int(np.ptp(qh)), int(np.ptp(qv))
+
+
+@pytest.mark.parametrize("point", DRIFT_SHAPES)
+def test_drift_points_leave_the_centred_label_range(point):
+    # the kept window really drifts (label sums beyond 64), while its width stays small
+    worst, wh, wv = label_sum_bound(point)
+    assert worst > 64 and wh < 40 and wv < 40
