@@ -24,6 +24,32 @@ import sys
 import time
 
 
+def phase_summary(H, delta, d_cut, temps, hbars, res, seconds, cv_prominence=0.0):
+    """JSON-ready summary of one hotrg_phase_scan: every C_V peak (with its height, its
+    prominence and whether a neighbouring sample has C_V < 0), the chi peak per central
+    field and the zero-field fit.  At small D_cut a change of the kept set between
+    beta - hb and beta + hb puts isolated spikes or dips into C_V's difference quotient;
+    a peak next to a negative C_V is such an artefact, not a transition."""
+    import numpy as np
+    temps = np.asarray(temps, dtype=np.float64)
+    cv = res["cv"]
+    cv_out = []
+    if cv is not None:
+        peaks, _ = H.hotrg_find_peaks(temps, cv, cv_prominence, len(temps))
+        for x, y, p in peaks:
+            k = int(np.argmin(np.abs(temps - x)))
+            neg = bool(np.any(cv[max(0, k - 1):k + 2] < 0))
+            cv_out.append({"T": x, "cv": y, "prominence": p, "next_to_negative_cv": neg})
+    f = res["fit"]
+    return {"delta": delta, "field": {H.T_IMP_M: "h", H.T_IMP_M1: "h1"}.get(res["field"], None), "d_cut": d_cut,
+            "seconds": seconds, "cv_peaks": cv_out, "hbar": list(hbars),
+            "T_chi_peak": [None if np.isnan(v) else float(v) for v in res["t_peak"]],
+            "T_c_zero_field": None if f.n == 0 else f.a,
+            "fit": None if f.n == 0 else {"a": f.a, "b": f.b, "c": f.c, "a_err": f.a_err, "b_err": f.b_err,
+                                          "c_err": f.c_err, "n": f.n, "at_bound": f.at_bound},
+            "status": res["status"]}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="paper_2609_20536_b300.cli")
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -66,6 +92,8 @@ def main(argv=None):
     ph.add_argument("--steps", type=int, default=30)
     ph.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     ph.add_argument("--nstreams", type=int, default=0)
+    ph.add_argument("--chi-prominence", type=float, default=0.0, help="least prominence of a chi peak")
+    ph.add_argument("--cv-prominence", type=float, default=0.0, help="least prominence of a listed C_V peak")
     c = sub.add_parser("contract")
     c.add_argument("--M", type=int, required=True)
     c.add_argument("--N", type=int, required=True)
@@ -170,23 +198,14 @@ def main(argv=None):
         base = H.params(1.0, a.delta, a.n_max, a.d_cut, a.steps, prec=prec,
                         block_sparse=1 if prec != H.FP64 else 0)
         t0 = time.perf_counter()
-        res = ctx.phase_scan(base, temps, hbars, field=field, dh=a.dh, nstreams=a.nstreams, check=False)
+        res = ctx.phase_scan(base, temps, hbars, field=field, dh=a.dh, nstreams=a.nstreams,
+                             min_prominence=a.chi_prominence, check=False)
         dt = time.perf_counter() - t0
         if res["status"] not in (H.OK, H.ENOCONV):
             print(json.dumps({"status": res["status"], "error": H.hotrg_last_error(ctx.handle)}))
             ctx.close()
             return 1
-        cv_peaks, _ = H.hotrg_find_peaks(temps, res["cv"], 0.0, 2)
-        f = res["fit"]
-        print(json.dumps({"delta": a.delta, "field": {H.T_IMP_M: "h", H.T_IMP_M1: "h1"}[res["field"]],
-                          "d_cut": a.d_cut, "seconds": dt,
-                          "T_cv_peaks": [x for x, _, _ in cv_peaks],
-                          "hbar": hbars, "T_chi_peak": [None if np.isnan(v) else v for v in res["t_peak"]],
-                          "T_c_zero_field": None if f.n == 0 else f.a,
-                          "fit": None if f.n == 0 else {"a": f.a, "b": f.b, "c": f.c, "a_err": f.a_err,
-                                                         "b_err": f.b_err, "c_err": f.c_err,
-                                                         "at_bound": f.at_bound},
-                          "status": res["status"]}))
+        print(json.dumps(phase_summary(H, a.delta, a.d_cut, temps, hbars, res, dt, a.cv_prominence)))
     else:
         g = torch.Generator(device="cuda").manual_seed(0)
         A = torch.randn(a.M, a.K, dtype=torch.float64, device="cuda", generator=g)

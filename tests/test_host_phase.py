@@ -117,3 +117,26 @@ def test_fit_rejects_bad_input(H):
                          (HB, np.where(HB > 0.02, np.nan, HB), 0.0, 0.0)):
         with pytest.raises(H.HotrgError):
             H.hotrg_fit_tc(h, t, lo, hi)
+
+
+def test_cli_phase_summary_flags_truncation_artefacts(H):
+    # a smooth C_V bump at T = 0.95 and an isolated dip to a negative value at T = 0.61,
+    # the shape a change of the kept set between beta -+ hb leaves in the difference quotient
+    import json
+    from paper_2609_20536_b300.cli import phase_summary
+    temps = np.linspace(0.55, 1.15, 41)
+    cv = 2.2 - 8.0 * (temps - 0.95) ** 2
+    cv[4] = -22.0
+    fit = H.hotrg_fit_tc(HB[:4], 0.9 + 0.8 * HB[:4] ** 0.4)
+    res = {"cv": cv, "t_peak": np.array([1.01, np.nan]), "fit": fit, "field": H.T_IMP_M, "status": 0}
+    out = phase_summary(H, 0.8, 24, temps, [0.005, 0.04], res, 1.0)
+    json.dumps(out)
+    peaks = out["cv_peaks"]
+    assert [p["next_to_negative_cv"] for p in peaks] == [True, False]
+    assert abs(peaks[1]["T"] - 0.95) < 1e-12 and abs(peaks[1]["cv"] - 2.2) < 1e-12
+    assert out["T_chi_peak"] == [1.01, None] and out["field"] == "h"
+    assert abs(out["T_c_zero_field"] - 0.9) < 1e-9 and out["fit"]["n"] == 4
+    # prominences 0.27 (the sample before the dip) and 0.32 (the bump): 0.3 keeps the bump; no fit gives null
+    res["fit"] = H.TcFit()
+    out = phase_summary(H, 0.8, 24, temps, [0.005, 0.04], res, 1.0, cv_prominence=0.3)
+    assert len(out["cv_peaks"]) == 1 and out["fit"] is None and out["T_c_zero_field"] is None
