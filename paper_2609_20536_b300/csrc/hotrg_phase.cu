@@ -221,7 +221,7 @@ hotrg_status hotrg_fit_tc(const double* hbar, const double* t_peak, int32_t n, d
         double best = INFINITY;
         std::vector<double> grid(FIT_GRID);
         for (int k = 0; k < FIT_GRID; ++k) {
-            grid[k] = lo + (hi - lo) * k / (FIT_GRID - 1);
+            grid[k] = k == FIT_GRID - 1 ? hi : lo + (hi - lo) * k / (FIT_GRID - 1);
             const double r = lin_fit(lh, t_peak, grid[k], z).rss;
             if (r < best) {
                 best = r;

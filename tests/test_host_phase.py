@@ -104,6 +104,11 @@ def test_fit_bounds_and_fixed_exponent(H):
     same_fit(f, OP.fit_tc(HB, t, 1.0, 1.0))
     slope, icpt = np.polyfit(HB, t, 1)
     assert abs(f.a - icpt) < 1e-12 and abs(f.b - slope) < 1e-10
+    # a minimum on the upper bound of an explicit bracket reports the bound exactly
+    t = 0.7 + 50.0 * HB ** 3.0
+    for hi in (1.7, 1.9, 2.3):
+        f = H.hotrg_fit_tc(HB, t, 0.1, hi)
+        assert f.at_bound == 1 and f.c == hi
     # a narrower bracket given explicitly
     t = 0.74 + 0.9 * HB ** 0.45 + 2e-3 * rng.standard_normal(len(HB))
     same_fit(H.hotrg_fit_tc(HB, t, 0.2, 0.8), OP.fit_tc(HB, t, 0.2, 0.8))
