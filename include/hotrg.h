@@ -59,7 +59,7 @@ typedef enum {
     HOTRG_ECUDA = -3,    /* a CUDA runtime call or kernel launch failed */
     HOTRG_ENOCONV = -4,  /* eigensolver (sweep cap) or zero-field fit did not converge */
     HOTRG_ETIMEOUT = -5, /* a bounded device wait ran out */
-    HOTRG_ENOTSUP = -6   /* form not available in this build / on this device */
+    HOTRG_ENOTSUP = -6   /* form not available in this build / on this device, or block labels too wide */
 } hotrg_status;
 
 typedef enum { HOTRG_FP64 = 0, HOTRG_SPLIT_BF16 = 1, HOTRG_SPLIT_BF16_FAST = 2 } hotrg_prec;
@@ -96,7 +96,10 @@ typedef struct {
                              run per charge block (the U(1) or Z2 structure of the block-sparse remark
                              of §2.3.1); split forms only, and only pure runs: with an impurity tensor
                              or h != 0 it has no effect.  The result equals the dense form's up to the
-                             split form's rounding. */
+                             split form's rounding.  The planner's value table follows each product's
+                             label range (kept charge windows may drift far from 0); a product whose
+                             signed label sums span 128 or more values stops the run with
+                             HOTRG_ENOTSUP. */
     int32_t gxy_q;       /* order q of the second coupling (1 - Delta) cos(q theta): 0 or 2 = the
                             thesis's q = 2 model; 1, 3, 4 the generalisations it names as future
                             work, a_n = sum_m I_{n - q m}(beta Delta) I_m(beta (1 - Delta)).  The
