@@ -157,3 +157,28 @@ def test_tiny_scan_moves_the_peak_with_the_field():
     assert tp[0] < tp[1] < tp[2]
     f = OP.fit_tc(hbars, tp)
     assert f["a"] < tp[0] and f["b"] > 0
+
+
+def test_ising_cv_matches_onsager_and_its_peak_locates_tc():
+    # The 2D Ising model is solved exactly (Onsager): away from T_c the C_V difference
+    # quotient of the HOTRG oracle equals that of the exact ln Z / N, and the refined C_V
+    # peak of a temperature scan sits at T_c = 2 / ln(1 + sqrt 2) to well within the grid
+    # spacing (the lattice of 2^24 sites and D_cut = 12 shift it by ~3e-4).
+    from oracle import exact, gxy
+    from oracle import hotrg as OH
+    hb = 1e-2
+
+    def cv_of(lnz_fn, T):
+        b = 1.0 / T
+        return b * b * (lnz_fn(b + hb) - 2.0 * lnz_fn(b) + lnz_fn(b - hb)) / hb ** 2
+
+    def hotrg_lnz(steps, dcut):
+        return lambda b: OH.hotrg_run(gxy.ising_tensor(b), gxy.ising_charges(), steps, dcut, "z2").lnz_per_site
+
+    for T in (1.8, 3.0):
+        assert abs(cv_of(hotrg_lnz(24, 16), T) - cv_of(exact.onsager_lnz, T)) < 1e-5
+    tc = 2.0 / math.log(1.0 + math.sqrt(2.0))
+    temps = np.linspace(2.22, 2.32, 11)
+    cv = [cv_of(hotrg_lnz(24, 12), T) for T in temps]
+    (t_peak, _, _), = OP.find_peaks(temps, cv, min_prominence=0.1)
+    assert abs(t_peak - tc) < 2e-3
