@@ -1324,7 +1324,10 @@ hotrg_status umma_check_status(hotrg_ctx* ctx) {
     HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     if (h != 0) {
         cudaMemsetAsync(g_status, 0, 4, ctx->stream);
-        return set_err(ctx, (hotrg_status)h, "tensor-core engine: a bounded wait ran out");
+        return set_err(ctx, (hotrg_status)h,
+                       h == HOTRG_ENOTSUP ? "block planner: a product's label sums span more values than its table, "
+                                            "or a charge block is wider than the slice pitch"
+                                          : "tensor-core engine: a bounded wait ran out");
     }
     return HOTRG_OK;
 }
