@@ -5,6 +5,11 @@ The compute path is the C-ABI library ``libhotrg.so`` (CUDA, built from
 ctypes binding with the same entry-point names.  Importing this package does
 not load the library; ``from paper_2609_20536_b300 import hotrg`` does, and
 fails loudly when it is missing.
+
+Modules: :mod:`.hotrg` (binding: points, batches, observables, phase-boundary
+scans, surrogate), :mod:`.cli` (command line), :mod:`.replicas` (sharding of
+independent points over ranks), :mod:`.workloads` (synthetic inputs),
+:mod:`.build` (nvcc build).
 """
 
-__all__ = ["hotrg", "build", "workloads"]
+__all__ = ["hotrg", "build", "cli", "replicas", "workloads"]
