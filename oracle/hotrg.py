@@ -60,6 +60,13 @@ from . import gxy
 
 TIE_RTOL = 1e-9
 SIDE_RTOL = 1e-6
+# The strict widths: exact ties only (the rounding level of an FP64 eigensolve)
+# and a bare eps_2 < eps_1 comparison.  Every step records whether they would
+# have kept the same side and the same eigenpairs, and how close each decision
+# was to its threshold, so that the effect of the two widths above on a run can
+# be read off without a second run.
+STRICT_TIE_RTOL = 1e-12
+STRICT_SIDE_RTOL = 0.0
 
 
 @dataclass
@@ -72,6 +79,14 @@ class StepRecord:
     side: int  # 0 = left (U), 1 = right (V)
     ln_c: float
     kept: np.ndarray  # kept eigenvalues, in kept order
+    # diagnostics of the two decisions of the step (no effect on the result):
+    # strict_same: the strict widths keep the same side and the same (charge,
+    # rank) eigenpairs; side_margin = eps_2 / eps_1 - 1 (nan without E_R);
+    # cut_gap: smallest | |lam - lam_cut| - tie_rtol lam_max | / lam_max over the
+    # chosen side's eigenvalues, the distance of the tie decision from its edge
+    strict_same: bool = True
+    side_margin: float = float("nan")
+    cut_gap: float = float("inf")
 
 
 @dataclass
@@ -147,16 +162,33 @@ def select_kept(cands, Dp, tie_rtol=TIE_RTOL):
     return above + cluster[:need]
 
 
-def truncation(E, qf, Dp, tie_rtol=TIE_RTOL):
-    """(P, new charges, eps = discarded weight, kept eigenvalues) for one E."""
-    cands = sector_eigen(E, qf)
-    keep = select_kept(cands, Dp, tie_rtol)
+def _truncate(cands, keep):
     kept_set = set(keep)
     eps = math.fsum(cands[a][0] for a in range(len(cands)) if a not in kept_set)
     P = np.stack([cands[a][3] for a in keep], axis=1)
     qn = np.array([cands[a][1] for a in keep], dtype=np.int64)
     kept = np.array([cands[a][0] for a in keep])
     return P, qn, eps, kept
+
+
+def truncation(E, qf, Dp, tie_rtol=TIE_RTOL):
+    """(P, new charges, eps = discarded weight, kept eigenvalues) for one E."""
+    cands = sector_eigen(E, qf)
+    return _truncate(cands, select_kept(cands, Dp, tie_rtol))
+
+
+def _labels(cands, keep):
+    return sorted((cands[a][1], cands[a][2]) for a in keep)
+
+
+def _cut_gap(cands, Dp, tie_rtol):
+    """Distance of the nearest eigenvalue from the edge of the cut cluster, / lam_max."""
+    if len(cands) <= Dp:
+        return float("inf")
+    lam = np.array([c[0] for c in cands])
+    lam_max = float(np.max(np.abs(lam)))
+    lam_cut = np.sort(lam)[::-1][Dp - 1]
+    return float(np.min(np.abs(np.abs(lam - lam_cut) - tie_rtol * lam_max)) / lam_max)
 
 
 def coarse(P3, T_up, T_dn):
@@ -166,7 +198,8 @@ def coarse(P3, T_up, T_dn):
     return _einsum("xrusd,rsy->xyud", Z, P3)      # s3
 
 
-def hotrg_step(T, qh, qv, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL, T_imp=None):
+def hotrg_step(T, qh, qv, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL, T_imp=None,
+               side_rtol=SIDE_RTOL):
     """One coarse-graining step.
 
     T has shape (Dh, Dh, Dv, Dv) = [l, r, u, d]; qh / qv are the integer labels
@@ -179,14 +212,26 @@ def hotrg_step(T, qh, qv, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL, T_im
     qf = fused_charges(qh, sym)
 
     EL = environment_left(T)
-    P, qn, eps_l, kept = truncation(EL, qf, Dp, tie_rtol)
+    cands = sector_eigen(EL, qf)
+    keep = select_kept(cands, Dp, tie_rtol)
+    P, qn, eps_l, kept = _truncate(cands, keep)
     eps_r = float("nan")
     side = 0
+    side_strict = 0
+    chosen = (cands, keep)
     if env_policy == 0:
         ER = environment_right(T)
-        PR, qnR, eps_r, keptR = truncation(ER, qf, Dp, tie_rtol)
-        if eps_r < eps_l * (1.0 - SIDE_RTOL):
+        candsR = sector_eigen(ER, qf)
+        keepR = select_kept(candsR, Dp, tie_rtol)
+        PR, qnR, eps_r, keptR = _truncate(candsR, keepR)
+        if eps_r < eps_l * (1.0 - side_rtol):
             P, qn, kept, side = PR, qnR, keptR, 1
+            chosen = (candsR, keepR)
+        side_strict = 1 if eps_r < eps_l * (1.0 - STRICT_SIDE_RTOL) else 0
+    cc, ck = chosen
+    strict_same = side_strict == side and (
+        _labels(cc, select_kept(cc, Dp, STRICT_TIE_RTOL)) == _labels(cc, ck))
+    side_margin = eps_r / eps_l - 1.0 if (env_policy == 0 and eps_l != 0.0) else float("nan")
 
     P3 = P.reshape(Dh, Dh, Dp)
     Tn = coarse(P3, T, T)
@@ -194,7 +239,8 @@ def hotrg_step(T, qh, qv, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL, T_im
     Tn = Tn / c
     T_next = np.ascontiguousarray(Tn.transpose(2, 3, 0, 1))
     rec = StepRecord(Dh=Dh, Dv=Dv, Dp=Dp, eps_left=eps_l, eps_right=eps_r, side=side,
-                     ln_c=math.log(c), kept=kept)
+                     ln_c=math.log(c), kept=kept, strict_same=strict_same, side_margin=side_margin,
+                     cut_gap=_cut_gap(cc, Dp, tie_rtol))
     imp_next = None
     if T_imp is not None:
         Ti = 0.5 * (coarse(P3, T_imp, T) + coarse(P3, T, T_imp)) / c
@@ -208,7 +254,7 @@ def trace(T):
 
 
 def hotrg_run(T0, q0, n_steps, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL,
-              T_imp0=None) -> RunResult:
+              T_imp0=None, side_rtol=SIDE_RTOL, on_step=None) -> RunResult:
     """n_steps of HOTRG from site tensor T0 (all four legs labelled q0).
 
     Returns ln Z / N for N = 2^n_steps sites, per-step records, and (with an
@@ -222,8 +268,10 @@ def hotrg_run(T0, q0, n_steps, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL,
     steps = []
     acc = math.log(c0)
     for k in range(1, n_steps + 1):
-        T, qh, qv, rec, Ti = hotrg_step(T, qh, qv, d_cut, sym, env_policy, tie_rtol, Ti)
+        T, qh, qv, rec, Ti = hotrg_step(T, qh, qv, d_cut, sym, env_policy, tie_rtol, Ti, side_rtol)
         steps.append(rec)
+        if on_step is not None:
+            on_step(k, rec)
         acc += rec.ln_c * 2.0 ** (-k)
     tr = trace(T)
     if not tr > 0.0:
@@ -236,7 +284,7 @@ def hotrg_run(T0, q0, n_steps, d_cut, sym="u1", env_policy=0, tie_rtol=TIE_RTOL,
 
 
 def run_gxy(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, env_policy=0,
-            impurity=None, tie_rtol=TIE_RTOL, q=2) -> RunResult:
+            impurity=None, tie_rtol=TIE_RTOL, q=2, side_rtol=SIDE_RTOL, on_step=None) -> RunResult:
     """Convenience: build the gXY tensor (and an impurity) and run HOTRG."""
     sym = gxy.symmetry_of(h, h1)
     T0 = gxy.site_tensor(beta, delta, n_max, h, h1, gxy.PURE, q=q)
@@ -244,4 +292,4 @@ def run_gxy(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, env_policy=0,
     if impurity is not None:
         Ti = gxy.site_tensor(beta, delta, n_max, h, h1, impurity, q=q)
     q0 = gxy.leg_charges(n_max, sym)
-    return hotrg_run(T0, q0, n_steps, d_cut, sym, env_policy, tie_rtol, Ti)
+    return hotrg_run(T0, q0, n_steps, d_cut, sym, env_policy, tie_rtol, Ti, side_rtol, on_step)
