@@ -2,25 +2,31 @@
 """HOTRG (beta, Delta) points/s at D_cut = 64 on B300.
 
 Workload: distinct (beta, Delta) points of the q = 2 generalized XY model,
-beta ~ U[0.5, 2.0], Delta ~ U[0, 1] (seed 20536), n_max = 4 (D0 = 9),
-D_cut = 64, 25 coarse-graining steps per point (2^25 sites), run through the
-C-ABI library (hotrg_run_batch on worker streams) in the split-BF16
-precision form with block-sparse (per U(1) charge block) contractions.  One bench step =
-one pass of the whole hot path (initial tensor, 25 HOTRG steps, closing
-trace) over `--points` points per GPU.  Several GPUs run independent
-replicas on distinct points (no collective on the data path).
+beta ~ U[0.5, 2.0], Delta ~ U[0, 1] (seed 20536, drawn one point at a time),
+n_max = 4 (D0 = 9), D_cut = 64, 25 coarse-graining steps per point (2^25
+sites), run through the C-ABI library (hotrg_run_batch on worker streams) in
+the split-BF16 precision form with block-sparse (per U(1) charge block)
+contractions.  One bench step = one pass of the whole hot path (initial
+tensor, 25 HOTRG steps, closing trace) over `--points` points per GPU.
+Several GPUs run independent replicas on distinct points (no collective on
+the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--points P] [--impl ours|reference]
 
-`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
-workload (the oracle is test infrastructure; this is its only use here).
+Besides the timed line: the plain FP64 form (block-sparse, FP64 FMA per
+charge block) runs every timed point in full, which gives both the FP64-form
+throughput and |d ln Z/N| of every timed point; the dense split and dense FP64
+forms run one full point each; the timed form is compared with the stored
+oracle results at D_cut = 64 (tests/golden); the FP64 CPU oracle is timed on a
+bounded sample.  `--impl reference` times that oracle sample as the reference
+arm (the oracle is test infrastructure; these are its only uses here).
 """
 
 import argparse
 import ctypes
+import glob
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -38,8 +44,15 @@ D_CUT, N_MAX, N_STEPS = 64, 4, 25
 WORKLOAD = ("gXY q=2 HOTRG points, beta~U[0.5,2.0], Delta~U[0,1] (seed 20536), n_max=4 (D0=9), "
             "D_cut=64, 25 one-axis steps per point (2^25 sites), split-BF16 tensor-core form")
 WORKLOAD_BS = ", contractions per U(1) charge block"
-# ncu DRAM traffic of the coarse-contraction kernel, keyed by the source hash it was captured on
-KNOWN_TRAFFIC = {}
+# ncu DRAM traffic of the grouped coarse-contraction kernel (s1, s2, s3 of one full-size
+# step), keyed by the hash of the kernel sources it was captured on: bytes per launch and
+# the algorithmic bytes of the same launches (profiles/traffic_umma_grouped_dcut64.md)
+KNOWN_TRAFFIC = {
+    "824c28ce1b50b8aa": {"dram_to_algorithmic": 2.3555, "dram_bytes_per_full_step_launch": 1.6135e9,
+                         "algorithmic_bytes_per_full_step_launch": 0.6850e9,
+                         "source": "profiles/traffic_umma_grouped_dcut64.md (ncu dram__bytes_read/write.sum, "
+                                   "the three coarse launches of a full-size D_cut=64 step)"},
+}
 
 
 def parse():
@@ -49,13 +62,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--points", type=int, default=2, help="points per bench step per GPU")
     ap.add_argument("--nstreams", type=int, default=0,
-                    help="worker streams of the batch runner (0: autotuned over 1..min(3, points) before the warm-up; "
-                         "1: points one after another on one stream)")
+                    help="worker streams of the batch runner (0: autotuned over 1..min(max-streams, points) before "
+                         "the warm-up; 1: points one after another on one stream)")
+    ap.add_argument("--max-streams", type=int, default=4, help="largest worker-stream count the autotuner tries")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     ap.add_argument("--block-sparse", type=int, default=1, choices=[0, 1],
-                    help="1: coarse contraction per U(1) charge block (the default form); 0: dense")
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-form, accuracy and CPU legs")
+                    help="1: contractions per U(1) charge block (the default form); 0: dense")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-form, dense-form, accuracy and CPU legs")
+    ap.add_argument("--no-dense-fp64", action="store_true", help="skip the one dense FP64 point (~4 min)")
     return ap.parse_args()
 
 
@@ -63,8 +79,8 @@ def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         d = json.load(open(path))
-        return d["bf16_tflops"], d["bf16_tflops_sustained"], "measured"
-    return 1800.0, 1400.0, "fallback"
+        return d["bf16_tflops"], d["bf16_tflops_sustained"], d.get("hbm_gbs", 6465.2), "measured"
+    return 1800.0, 1400.0, 6400.0, "fallback"
 
 
 class Clocks:
@@ -117,55 +133,83 @@ class Clocks:
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ["hotrg_umma.cu", "internal.cuh"]:
+    for f in ["hotrg_umma.cu", "hotrg_blocks.cu", "internal.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_2609_20536_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------------------
+# Algorithmic (dense) work of a point, the unit of the CPU oracle's samples
+# ---------------------------------------------------------------------------
+def step_sizes(d0=2 * N_MAX + 1, d_cut=D_CUT, n_steps=N_STEPS):
+    h = v = d0
+    out = []
+    for _ in range(n_steps):
+        dp = min(d_cut, h * h)
+        out.append((h, v, dp))
+        h, v = v, dp
+    return out
+
+
+def step_flops(Dh, Dv, Dp):
+    """Dense flops of one step as the oracle computes it: both environments (A, B, E,
+    Eq. 2.12 regrouped) and the coarse contraction s1, s2, s3 (Eq. 2.16)."""
+    env = 2 * (2 * 2 * Dh ** 3 * Dv ** 3 + 2 * Dh ** 4 * Dv ** 2)
+    coarse = 2 * Dp * Dh ** 3 * Dv ** 2 + 2 * Dp * Dh ** 3 * Dv ** 3 + 2 * Dp ** 2 * Dh ** 2 * Dv ** 2
+    return float(env), float(coarse)
+
+
+def point_flops():
+    return sum(sum(step_flops(*s)) for s in step_sizes())
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_point_seconds(beta, delta, nx=4):
-    """Seconds per point of the FP64 oracle, from a bounded sample.
+def oracle_sample(beta, delta, nx=4):
+    """One bounded sample of a point's work on the FP64 oracle, timed in full.
 
-    Steps 1 and 2 run in full.  Step 3 is the first step at full size
-    (D_h = D_v = D' = 64) and every later step has the same size: its
-    environments and truncations are timed in full, its coarse contraction on
-    nx of the D' output columns x (the contraction is linear in that count),
-    scaled by D'/nx.  Per point = t1 + t2 + (n_steps - 2) x t3.
+    Steps 1 and 2 run in full.  Step 3 (the first at full size, D_h = D_v =
+    D' = 64, like every later step) runs its two environments and
+    truncations in full and its coarse contraction on nx of the D' output
+    columns x, then the norm.  Returns (seconds, units, detail): units is the
+    sample's share of a whole point's algorithmic flops (the flop model of
+    step_flops, the eigensolves not counted), so units / seconds is the
+    oracle's throughput in points/s.
     """
     import numpy as np
     from oracle import gxy
     from oracle import hotrg as OH
 
+    t_all = time.perf_counter()
     T = gxy.site_tensor(beta, delta, N_MAX)
     T = T / np.linalg.norm(T)
     q = gxy.leg_charges(N_MAX, "u1")
     qh, qv = q.copy(), q.copy()
-    t_steps = []
     for _ in range(2):
-        t0 = time.perf_counter()
         T, qh, qv, _, _ = OH.hotrg_step(T, qh, qv, D_CUT, "u1")
-        t_steps.append(time.perf_counter() - t0)
-    Dh = T.shape[0]
+    Dh, Dv = T.shape[0], T.shape[2]
     Dp = min(D_CUT, Dh * Dh)
     qf = OH.fused_charges(qh, "u1")
     t0 = time.perf_counter()
     EL = OH.environment_left(T)
     ER = OH.environment_right(T)
-    P, _, eps_l, _ = OH.truncation(EL, qf, Dp)
+    P, _, _, _ = OH.truncation(EL, qf, Dp)
     OH.truncation(ER, qf, Dp)
     t_env = time.perf_counter() - t0
     P3 = P.reshape(Dh, Dh, Dp)
     t0 = time.perf_counter()
     Tn = OH.coarse(np.ascontiguousarray(P3[:, :, :nx]), T, T)  # nx of the D' left output columns
-    t_coarse = (time.perf_counter() - t0) * Dp / nx
-    t0 = time.perf_counter()
     float(np.linalg.norm(Tn))
-    t_norm = (time.perf_counter() - t0) * Dp / nx
-    t3 = t_env + t_coarse + t_norm
-    return t_steps[0] + t_steps[1] + (N_STEPS - 2) * t3, {"t_step1": t_steps[0], "t_step2": t_steps[1],
-                                                          "t_step3_est": t3, "x_columns": nx}
+    t_coarse = time.perf_counter() - t0
+    sec = time.perf_counter() - t_all
+    sizes = step_sizes()
+    work = sum(sum(step_flops(*s)) for s in sizes[:2])
+    env3, coarse3 = step_flops(*sizes[2])
+    work += env3 + coarse3 * nx / Dp
+    units = work / point_flops()
+    return sec, units, {"step3_env_trunc_s": t_env, "step3_coarse_s": t_coarse, "x_columns": nx,
+                        "units_per_sample": units}
 
 
 def blas_threads():
@@ -177,6 +221,12 @@ def blas_threads():
         return os.cpu_count()
 
 
+SAMPLE_TEXT = ("each sample: one point's steps 1-2 in full, then step 3 (full size, D=64) with both environments "
+               "and truncations in full and the coarse contraction on {nx} of 64 output columns; units = the "
+               "sample's share of a point's algorithmic flops (dense flop model of the oracle's contractions, "
+               "eigensolves uncounted)")
+
+
 def run_reference(args):
     from paper_2609_20536_b300.workloads import headline_points
     rank = int(os.environ.get("RANK", "0"))
@@ -184,24 +234,22 @@ def run_reference(args):
         return
     pts = headline_points(args.warmup + args.steps, d_cut=D_CUT, n_max=N_MAX, n_steps=N_STEPS)
     for p in pts[: args.warmup]:
-        oracle_point_seconds(p.beta, p.delta)
-    per_point = []
+        oracle_sample(p.beta, p.delta)
+    secs, units = 0.0, 0.0
     detail = None
     for p in pts[args.warmup:]:
-        s, detail = oracle_point_seconds(p.beta, p.delta)
-        per_point.append(s)
-    sec = statistics.mean(per_point)
-    value = 1.0 / sec
-    sample = ("per point: steps 1-2 in full, step 3 environments/truncation in full and its coarse "
-              "contraction on 4 of 64 output columns scaled x16, steps 3-25 taken equal (extrapolated)")
+        s, u, detail = oracle_sample(p.beta, p.delta)
+        secs += s
+        units += u
+    value = units / secs
     cores = blas_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("split-BF16 tensor-core form", "FP64 CPU oracle (numpy)"),
-                       "points_per_step": 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-                             "detail": detail},
+                       "samples_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": SAMPLE_TEXT.format(nx=4), "detail": detail},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -236,16 +284,19 @@ def main():
     n_total = (args.warmup + args.steps) * P * world
     pts = headline_points(n_total, d_cut=D_CUT, n_max=N_MAX, n_steps=N_STEPS)
 
-    def batch(step):
+    def batch_pts(step):
         base = (step * world + rank) * P
-        return [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec, block_sparse=args.block_sparse)
-                for p in pts[base:base + P]]
+        return pts[base:base + P]
+
+    def batch(step, pr=prec, bs=args.block_sparse):
+        return [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=pr, block_sparse=bs)
+                for p in batch_pts(step)]
 
     tuned = None
     if args.nstreams == 0:
         # autotune the worker-stream count on one bench step's worth of points (untimed); more
         # streams than points per step would only idle
-        best, secs = ctx.autotune_batch(batch(0), max_streams=max(1, min(3, P)))
+        best, secs = ctx.autotune_batch(batch(0), max_streams=max(1, min(args.max_streams, P)))
         tuned = {"chosen": best, "seconds_per_count": secs, "points": P}
         args.nstreams = best
 
@@ -277,6 +328,7 @@ def main():
     clk = clocks.stop()
     dev_ms = ev0.elapsed_time(ev1)
     prof = H.hotrg_profile_read(ctx.handle)
+    H.hotrg_profile_enable(ctx.handle, False)
     t = torch.tensor([dev_ms, wall], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -292,29 +344,8 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    burst, sustained, src = peaks()
-    coarse_ms = prof.gemm_ms[1]
-    fp64_equiv = prof.gemm_flops[1] / (coarse_ms / 1e3) / 1e12 if coarse_ms > 0 else 0.0
-    slices = 15 if prec == H.SPLIT_BF16 else (6 if prec == H.SPLIT_BF16_FAST else 1)
-    # a split form is bounded by the BF16 tensor pipe: every slice product is 2MNK of BF16 work
-    achieved = fp64_equiv * slices
-    kname = ("umma_grouped_kernel<5> (block-sparse coarse contraction s1/s2/s3)" if args.block_sparse
-             else "umma_gemm_kernel<5> (coarse contraction s1/s2/s3)")
-    roof = {"bound": "tensor", "kernel": kname,
-            "achieved": achieved, "peak": sustained, "unit": "TFLOP/s", "frac": achieved / sustained,
-            "peak_source": f"bf16 sustained, {src}",
-            "achieved_is": (f"{slices} BF16 slice products x 2MNK per contraction (per charge block, summed over "
-                            "blocks, when block-sparse) / CUDA-event time on its stream"),
-            "slice_products": slices, "fp64_equivalent_tflops": fp64_equiv,
-            "kernel_share_of_steps": coarse_ms / prof.step_ms if prof.step_ms else None,
-            "traffic": KNOWN_TRAFFIC.get(source_hash())}
-    breakdown = {"coarse_gemm_ms": coarse_ms, "env_gemm_ms": prof.gemm_ms[0], "slice_ms": prof.slice_ms,
-                 "eig_ms": prof.eig_ms, "eig_parts_ms": {"jacobi_small": prof.eig_part_ms[0],
-                                                          "subspace_fp32": prof.eig_part_ms[1],
-                                                          "rayleigh_ritz": prof.eig_part_ms[2],
-                                                          "select_projector": prof.eig_part_ms[3]},
-                 "steps_ms": prof.step_ms, "hotrg_steps": prof.steps,
-                 "note": "CUDA-event time per region class summed over worker streams (regions overlap in time)"}
+    timed = [p for s in range(args.warmup, args.warmup + args.steps) for p in batch_pts(s)]
+    roof, breakdown = roofline(H, prof, prec, args.block_sparse)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec != H.FP64 else "f64",
@@ -322,63 +353,139 @@ def main():
             "config": {"workload": WORKLOAD + (WORKLOAD_BS if args.block_sparse else ""), "points_per_step": P,
                        "worker_streams": args.nstreams, "autotune": tuned,
                        "d_cut": D_CUT, "n_max": N_MAX,
-                       "n_steps": N_STEPS, "prec": args.prec, "parallelism": f"replicas x{world}",
-                       "l2": "working set above L2: 8.6 GB D^5 intermediates per HOTRG step"},
+                       "n_steps": N_STEPS, "prec": args.prec, "block_sparse": args.block_sparse,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "working set above L2: D^5 intermediates (8.6 GB dense arrays) every HOTRG step"},
             "roofline": roof, "breakdown": breakdown, "clocks": clk, "gpu_launches": int(prof.launches),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": ctypes.sizeof(H.Params) * P * world,
                     "d2h_bytes_per_step": ctypes.sizeof(H.Result) * P * world,
                     "note": "host wall clock around the synchronous hotrg_run_batch / hotrg_run C-ABI call: "
                             "params in, results out"}}
     if not args.no_extras and world == 1:
-        line.update(extras(H, ctx, pts, prec, args.block_sparse))
+        line.update(extras(H, ctx, timed, results, prec, args, value))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def extras(H, ctx, pts, prec, bs):
-    """FP64-form and dense-form timing at the same D_cut, accuracy against the oracle, CPU oracle baseline."""
-    out = {}
+def roofline(H, prof, prec, bs):
+    """Roofline entry of the coarse-contraction GEMM plus per-kernel-class fractions."""
+    burst, sustained, hbm, src = peaks()
+    ns_coarse = 5 if prec == H.SPLIT_BF16 else (3 if prec == H.SPLIT_BF16_FAST else 1)
+    ns_env = 4 if prec == H.SPLIT_BF16 else (3 if prec == H.SPLIT_BF16_FAST else 1)
+    prods = lambda ns: ns * (ns + 1) // 2 if prec != H.FP64 else 1  # noqa: E731  BF16 slice products
+    coarse_ms, env_ms = prof.gemm_ms[1], prof.gemm_ms[0]
+    fp64_equiv = prof.gemm_flops[1] / (coarse_ms / 1e3) / 1e12 if coarse_ms > 0 else 0.0
+    achieved = fp64_equiv * prods(ns_coarse)
+    kname = ("umma_grouped_kernel<5> (block-sparse coarse contraction s1/s2/s3)" if bs
+             else "umma_gemm_kernel<5> (coarse contraction s1/s2/s3)")
+    traffic = KNOWN_TRAFFIC.get(source_hash())
+    calls = max(1, prof.gemm_calls[1])
+    # algorithmic bytes of one coarse launch: the BF16 slices of every operand element once,
+    # the output once (W, Z as FP32 pairs, T' in FP64: 8 bytes either way)
+    alg_bytes = (prof.operand_elems[1] * 2 * ns_coarse + prof.output_elems[1] * 8) / calls
+    roof = {"bound": "tensor", "kernel": kname,
+            "achieved": achieved, "peak": sustained, "unit": "TFLOP/s", "frac": achieved / sustained,
+            "peak_source": f"bf16 sustained, {src}",
+            "achieved_is": (f"{prods(ns_coarse)} BF16 slice products x 2MNK per contraction (per charge block, "
+                            "summed over blocks, when block-sparse) / CUDA-event time on its stream"),
+            "slice_products": prods(ns_coarse), "fp64_equivalent_tflops": fp64_equiv,
+            "kernel_share_of_steps": coarse_ms / prof.step_ms if prof.step_ms else None,
+            "algorithmic_bytes_per_launch": alg_bytes if bs else None,
+            # the ncu ratio of DRAM to algorithmic bytes at a full-size step, applied to this run's
+            # algorithmic bytes per coarse launch (traffic grows with the block elements processed)
+            "traffic": traffic["dram_to_algorithmic"] * alg_bytes if (traffic and bs) else None,
+            "traffic_source": traffic["source"] if traffic else "no ncu capture of this kernel build"}
+    kernels = {}
+    if env_ms > 0:
+        env_tf = prof.gemm_flops[0] / (env_ms / 1e3) / 1e12 * prods(ns_env)
+        kernels["env_grouped_gemm"] = {"bound": "tensor", "achieved_tflops": env_tf, "frac": env_tf / sustained,
+                                       "slice_products": prods(ns_env),
+                                       "share_of_steps": env_ms / prof.step_ms if prof.step_ms else None}
+    if prof.slice_ms > 0 and bs and prec != H.FP64:
+        # each operand element is read once (8 bytes: FP64 or an FP32 pair) and written as NS BF16 slices
+        sb = prof.operand_elems[0] * (8 + 2 * ns_env) + prof.operand_elems[1] * (8 + 2 * ns_coarse)
+        gbs = sb / (prof.slice_ms / 1e3) / 1e9
+        kernels["slicers"] = {"bound": "hbm", "achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm,
+                              "algorithmic_bytes": sb, "share_of_steps": prof.slice_ms / prof.step_ms}
+    if prof.steps:
+        kernels["eigensolve"] = {"bound": "latency", "ms_per_step": prof.eig_ms / prof.steps,
+                                 "share_of_steps": prof.eig_ms / prof.step_ms if prof.step_ms else None}
+    roof["kernels"] = kernels
+    breakdown = {"coarse_gemm_ms": coarse_ms, "env_gemm_ms": env_ms, "slice_ms": prof.slice_ms,
+                 "eig_ms": prof.eig_ms, "eig_parts_ms": {"jacobi_small": prof.eig_part_ms[0],
+                                                          "subspace_fp32": prof.eig_part_ms[1],
+                                                          "rayleigh_ritz": prof.eig_part_ms[2],
+                                                          "select_projector": prof.eig_part_ms[3]},
+                 "steps_ms": prof.step_ms, "hotrg_steps": prof.steps,
+                 "coarse_block_flops": prof.gemm_flops[1], "env_block_flops": prof.gemm_flops[0],
+                 "note": "CUDA-event time per region class summed over worker streams (regions overlap in time)"}
+    return roof, breakdown
+
+
+def extras(H, ctx, timed, results, prec, args, value):
+    """FP64 form and accuracy on every timed point, dense forms on one point each, the oracle
+    goldens, the CPU oracle baseline."""
     import torch
-    # FP64 form: first 3 steps of one point (step 3 is the first at full size)
-    p = pts[0]
+    out = {}
+    bs, ns = args.block_sparse, args.nstreams
+    # the plain FP64 form (per charge block when the timed form is) on every timed point, in full,
+    # through the same batch runner and stream count
+    fp = [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=H.FP64, block_sparse=bs) for p in timed]
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    r2 = ctx.run([H.params(p.beta, p.delta, p.n_max, p.d_cut, 2, prec=H.FP64)])[0]
-    t2 = time.perf_counter() - t0
+    rf = ctx.run_batch(fp, nstreams=ns) if ns > 1 else ctx.run(fp)
+    tf = time.perf_counter() - t0
+    fp_value = len(fp) / tf
+    out["fp64_form"] = {"value": fp_value, "unit": UNIT, "points": len(fp), "n_steps": N_STEPS,
+                        "block_sparse": bs, "worker_streams": ns, "s_per_point": tf / len(fp),
+                        "mixed_vs_fp64": value / fp_value,
+                        "note": "plain FP64 form (FP64 FMA contractions, FP64 Jacobi on every block) on the same "
+                                "points as the timed form, full length, host wall clock around the synchronous "
+                                "call"}
+    d = [r.lnz_per_site - f.lnz_per_site for r, f in zip(results, rf)]
+    acc = {"vs_fp64_form": {"max_abs_dlnz": max(abs(x) for x in d), "points": len(d), "d_cut": D_CUT,
+                            "n_steps": N_STEPS, "over_1e-9": sum(abs(x) > 1e-9 for x in d),
+                            "per_point": [float("%.3g" % x) for x in d]}}
+    # the stored oracle results (tests/golden, written by the FP64 CPU oracle alone)
+    gold = []
+    for f in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "oracle_*.json"))):
+        g = json.load(open(f))
+        r = ctx.run([H.params(g["beta"], g["delta"], g["n_max"], g["d_cut"], g["n_steps"], prec=prec,
+                              block_sparse=bs)])[0]
+        gold.append({"case": g["case"], "d_cut": g["d_cut"], "n_steps": g["n_steps"],
+                     "dlnz": r.lnz_per_site - g["lnz_per_site"]})
+    if gold:
+        acc["vs_oracle"] = {"max_abs_dlnz": max(abs(x["dlnz"]) for x in gold), "cases": gold}
+    out["accuracy"] = acc
+    # dense forms (every contraction over all elements), one full point each
+    q = timed[0]
+    dense = {}
     t0 = time.perf_counter()
-    r3 = ctx.run([H.params(p.beta, p.delta, p.n_max, p.d_cut, 3, prec=H.FP64)])[0]
-    t3 = time.perf_counter() - t0 - t2
-    fp64_point_s = t2 + (N_STEPS - 2) * t3
-    split3 = ctx.run([H.params(p.beta, p.delta, p.n_max, p.d_cut, 3, prec=prec, block_sparse=bs)])[0]
-    out["fp64_form"] = {"value": 1.0 / fp64_point_s, "unit": UNIT, "s_per_full_step": t3,
-                        "note": "FP64 SIMT form at the same workload, 3 steps timed, steps 3-25 taken equal",
-                        "dlnz_split_vs_fp64_after_3_steps": split3.lnz_per_site - r3.lnz_per_site}
-    if bs:
-        # the dense split form (every contraction over all elements) on one point, for comparison
-        q = pts[1]
+    rd = ctx.run([H.params(q.beta, q.delta, q.n_max, q.d_cut, q.n_steps, prec=prec)])[0]
+    td = time.perf_counter() - t0
+    dense["split"] = {"value": 1.0 / td, "dlnz_vs_block_form": rd.lnz_per_site - results[0].lnz_per_site}
+    if not args.no_dense_fp64:
         t0 = time.perf_counter()
-        rd = ctx.run([H.params(q.beta, q.delta, q.n_max, q.d_cut, q.n_steps, prec=prec)])[0]
-        td = time.perf_counter() - t0
-        rb = ctx.run([H.params(q.beta, q.delta, q.n_max, q.d_cut, q.n_steps, prec=prec, block_sparse=1)])[0]
-        out["dense_form"] = {"value": 1.0 / td, "unit": UNIT, "note": "split-BF16 form with dense contractions, "
-                             "one point, host wall clock", "dlnz_block_vs_dense": rb.lnz_per_site - rd.lnz_per_site}
-    # accuracy of the timed form against the FP64 oracle on smaller points of the same family
-    from oracle import hotrg as OH
-    errs = []
-    for q in pts[:3]:
-        ref = OH.run_gxy(q.beta, q.delta, q.n_max, 16, 20).lnz_per_site
-        got = ctx.run([H.params(q.beta, q.delta, q.n_max, 16, 20, prec=prec, block_sparse=bs)])[0].lnz_per_site
-        errs.append(abs(got - ref))
-    out["accuracy"] = {"max_abs_dlnz_vs_oracle": max(errs), "points": 3, "d_cut": 16, "n_steps": 20,
-                       "note": "same (beta, Delta) points at D_cut=16 (oracle at D_cut=64 takes ~30 min/point)"}
-    # CPU oracle baseline (bounded sample)
-    t0 = time.perf_counter()
-    sec, detail = oracle_point_seconds(p.beta, p.delta)
-    out["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                           "sample": ("one point: steps 1-2 in full, step 3 environments/truncation in full and "
-                                      "its coarse contraction on 4 of 64 output columns scaled x16, steps 3-25 "
-                                      "taken equal (extrapolated)"),
-                           "sample_wall_s": time.perf_counter() - t0, "detail": detail}
+        rdf = ctx.run([H.params(q.beta, q.delta, q.n_max, q.d_cut, q.n_steps, prec=H.FP64)])[0]
+        tdf = time.perf_counter() - t0
+        dense["fp64"] = {"value": 1.0 / tdf, "dlnz_vs_dense_split": rd.lnz_per_site - rdf.lnz_per_site}
+        dense["dense_split_vs_dense_fp64"] = tdf / td
+    dense["note"] = "one full point each, host wall clock around the synchronous call"
+    out["dense_form"] = dense
+    # CPU oracle baseline (bounded samples, all host cores and one)
+    s, u, detail = oracle_sample(timed[0].beta, timed[0].delta)
+    cpu = {"value": u / s, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+           "sample": SAMPLE_TEXT.format(nx=4), "sample_wall_s": s, "detail": detail}
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1):
+            s1, u1, _ = oracle_sample(timed[0].beta, timed[0].delta, nx=1)
+        cpu["single_core"] = {"value": u1 / s1, "unit": UNIT, "cores": 1, "sample": SAMPLE_TEXT.format(nx=1),
+                              "sample_wall_s": s1}
+    except ImportError:
+        pass
+    out["cpu_baseline"] = cpu
     torch.cuda.synchronize()
     return out
 

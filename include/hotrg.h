@@ -94,16 +94,27 @@ typedef struct {
                             the rounding of the eigenvalue sums */
     int32_t block_sparse; /* 1: the environments (A, B, E) and the coarse contraction (s1, s2, s3)
                              run per charge block (the U(1) or Z2 structure of the block-sparse remark
-                             of §2.3.1); split forms only, and only pure runs: with an impurity tensor
-                             or h != 0 it has no effect.  The result equals the dense form's up to the
-                             split form's rounding.  The planner's value table follows each product's
-                             label range (kept charge windows may drift far from 0); a product whose
-                             signed label sums span 128 or more values stops the run with
-                             HOTRG_ENOTSUP. */
+                             of §2.3.1), in every precision form (HOTRG_FP64: FP64 FMA per block);
+                             pure runs only: with an impurity tensor or h != 0 it has no effect.  The
+                             result equals the dense form's up to the rounding of the form (the FP64
+                             form sums each block's products in the same K order as the dense one, but
+                             over the block's elements only).  The planner's value table follows each
+                             product's label range (kept charge windows may drift far from 0); a
+                             product whose signed label sums span 128 or more values stops that point
+                             with HOTRG_ENOTSUP. */
     int32_t gxy_q;       /* order q of the second coupling (1 - Delta) cos(q theta): 0 or 2 = the
                             thesis's q = 2 model; 1, 3, 4 the generalisations it names as future
                             work, a_n = sum_m I_{n - q m}(beta Delta) I_m(beta (1 - Delta)).  The
                             tensor, its charge rule and every kernel are otherwise the same. */
+    int32_t eig_mode;    /* eigensolver of the truncation.  0: the form's default -- blocks of at most b
+                            states (the listed width) by FP64 Jacobi; larger blocks list b eigenpairs by
+                            block subspace iteration: FP32 iterations, then an FP64 Rayleigh-Ritz step,
+                            then eig_fp64_iters FP64 subspace iterations each with its Rayleigh-Ritz step
+                            (the FP64 form uses this path for U(1) labels and Jacobi on every block for
+                            Z2 or no symmetry).  1: FP64 Jacobi on every block (all eigenpairs). */
+    int32_t eig_fp64_iters; /* FP64 subspace iterations after the first Rayleigh-Ritz step: 0 = the
+                               form's default (3 for HOTRG_FP64, none for the split forms), 1..8 that
+                               many, -1 none */
 } hotrg_params;
 
 /* Per-step scalars (device- or host-resident, see each entry point). */
@@ -114,7 +125,8 @@ typedef struct {
     int32_t side;      /* 0: projector from E_L; 1: from E_R */
     int32_t dprime;    /* D' = min(D_cut, D_h^2) */
     int32_t sweeps;    /* largest Jacobi sweep count over the sectors */
-    int32_t status;    /* hotrg_status of the device part of the step */
+    int32_t status;    /* hotrg_status of the device part of the step: the eigensolver's, else a
+                          contraction engine failure (HOTRG_ETIMEOUT, HOTRG_ENOTSUP) */
 } hotrg_step_info;
 
 /* Result of one point. */
@@ -187,7 +199,9 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, const hotrg_params* p,
  * imp_kind = HOTRG_T_IMP_M or HOTRG_T_IMP_M1 each point also carries that
  * impurity tensor and reports imp_ratio; HOTRG_T_PURE runs the pure tensor
  * only.  Returns the first non-OK point status (each out[i].status holds
- * its own).  Synchronous. */
+ * its own: a device-side failure -- a bounded wait that ran out, a block
+ * plan that overflowed -- is recorded in a status slot of that point's own
+ * device result block and fails that point alone).  Synchronous. */
 hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
                        int32_t imp_kind, hotrg_result* out);
 
@@ -206,7 +220,11 @@ hotrg_status hotrg_run(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoin
  * its worker's stream and added to the context's counters.
  * nstreams = 0 takes the count chosen by hotrg_autotune_batch (2 if untuned).
  * params, out: host arrays of npoints.  Synchronous.  Returns the first
- * non-OK status (each out[i].status holds its own). */
+ * non-OK status (each out[i].status holds its own).  A point that fails on
+ * the host (invalid parameters) or on the device (its own status slot, as in
+ * hotrg_run, also inside a replayed graph) fails alone; the other points'
+ * results are unaffected.  Only a failure of the batch machinery itself
+ * (stream, graph or pinned-memory calls) fails every point. */
 hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t npoints,
                              int32_t imp_kind, int32_t nstreams, hotrg_result* out);
 
@@ -264,8 +282,12 @@ hotrg_status hotrg_contract(hotrg_ctx* ctx, int32_t prec, int32_t M, int32_t N, 
  *   HOTRG_SPLIT_BF16 or HOTRG_SPLIT_BF16_FAST, work on cuda_stream (a
  *   cudaStream_t, NULL for the legacy default stream).  The call returns
  *   after C is written (it synchronises the stream to read the status word).
- * Size limit: with NS = 5 (HOTRG_SPLIT_BF16) or 3 (_FAST), Kp = K rounded up
- * to 32, Mp and Np = M and N rounded up to 128, the call needs
+ * NS is the slice count of the form's coarse contraction, as in
+ * hotrg_contract: 5 for HOTRG_SPLIT_BF16 (the environment variable
+ * HOTRG_SPLIT_SLICES="e,c", read once per process, sets it to c in 3..5, which
+ * changes both the accuracy and the size limit below) and 3 for _FAST.
+ * Size limit: with Kp = K rounded up to 32, Mp and Np = M and N rounded up to
+ * 128, the call needs
  * NS (Mp + Np) Kp 2 + 4 (Mp + Np) bytes (each term rounded up to 256) plus
  * 256; above 32 MiB it returns HOTRG_EINVAL without launching anything.
  * The first call on each device looks up the device address of the static
@@ -454,6 +476,12 @@ typedef struct {
     double step_ms;
     int64_t steps;
     double eig_part_ms[4]; /* block discovery + Jacobi; FP32 subspace; FP64 Rayleigh-Ritz; selection + projector */
+    /* Block-sparse products only (counted on the device by the block planner), per class:
+     * operand_elems = sum over blocks of (M_g + N_g) K_g, the operand elements a product reads
+     * once (what the slicers of the split forms read as 8 bytes and write as NS BF16 slices);
+     * output_elems = sum over blocks of M_g N_g, the elements it writes. */
+    double operand_elems[3];
+    double output_elems[3];
 } hotrg_profile;
 
 /* Turn event timing on (enable != 0) or off, and reset the counters.

@@ -5,6 +5,7 @@
   python -m paper_2609_20536_b300.cli grid --n 64 [--nstreams 0]
   python -m paper_2609_20536_b300.cli surrogate [--nb 12 --nd 8 --d-cut 12 --steps 16]
   python -m paper_2609_20536_b300.cli phase --delta 0.32 [--t-lo 0.5 --t-hi 1.2 --n-t 36 --hbar 0.005,0.01,0.02,0.04]
+  python -m paper_2609_20536_b300.cli peaks
 
 `run` prints ln Z/N and the per-step scalars of one point; `grid` times a
 sample of the 64 x 64 (beta, Delta) grid with D_cut drawn from {24, 32, 48,
@@ -13,7 +14,9 @@ observables, trains the MLP ensemble, audits it against HOTRG on random
 points and refines near the C_V / chi maxima; `phase` scans one Delta in
 temperature and prints the C_V peaks, the chi peak at each central field and
 the zero-field T_c of the fit T_p = a + b hbar^c (a row of Table 3.1 at this
-bond dimension); `contract` times one C = A B^T of the given
+bond dimension); `peaks` measures cuBLAS's dense GEMM rates (torch.matmul)
+in FP64, FP32, TF32 and BF16, the denominators of the FP64-form rooflines;
+`contract` times one C = A B^T of the given
 shape through the contraction engine (random FP64 operands generated on the
 device).
 """
@@ -63,12 +66,17 @@ def main(argv=None):
     r.add_argument("--h1", type=float, default=0.0)
     r.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     r.add_argument("--block-sparse", type=int, default=1, choices=[0, 1])
+    r.add_argument("--profile", action="store_true", help="also print the library's per-class profile counters")
     g = sub.add_parser("grid")
     g.add_argument("--n", type=int, default=64, help="first n points of the 64 x 64 (beta, Delta) grid")
     g.add_argument("--stride", type=int, default=61, help="take every stride-th grid point (spreads beta, Delta)")
     g.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
     g.add_argument("--block-sparse", type=int, default=1, choices=[0, 1])
     g.add_argument("--nstreams", type=int, default=0, help="0: autotune 1..4 worker streams on 8 points first")
+    g.add_argument("--check", type=int, default=0,
+                   help="re-run this many of the points (spread over the sample) in the FP64 block form and "
+                        "report |d lnZ/N| against it")
+    g.add_argument("--out", default="", help="write every point's (beta, Delta, D_cut, lnZ/N, status) as JSON here")
     sg = sub.add_parser("surrogate")
     sg.add_argument("--nb", type=int, default=12, help="training grid: nb betas in [0.6, 1.6]")
     sg.add_argument("--nd", type=int, default=8, help="training grid: nd Deltas in [0.1, 0.9]")
@@ -94,6 +102,8 @@ def main(argv=None):
     ph.add_argument("--nstreams", type=int, default=0)
     ph.add_argument("--chi-prominence", type=float, default=0.0, help="least prominence of a chi peak")
     ph.add_argument("--cv-prominence", type=float, default=0.0, help="least prominence of a listed C_V peak")
+    pk = sub.add_parser("peaks")
+    pk.add_argument("--repeat", type=int, default=5)
     c = sub.add_parser("contract")
     c.add_argument("--M", type=int, required=True)
     c.add_argument("--N", type=int, required=True)
@@ -105,19 +115,52 @@ def main(argv=None):
     import torch
     from . import hotrg as H
 
+    if a.cmd == "peaks":
+        # dense n^3 matmuls through cuBLAS (torch): 3 warm-ups, best of --repeat, CUDA events
+        out = {}
+        for name, dt, n in (("fp64", torch.float64, 4096), ("fp32", torch.float32, 8192),
+                            ("tf32", torch.float32, 8192), ("bf16", torch.bfloat16, 8192)):
+            torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+            x = torch.randn(n, n, device="cuda", dtype=dt)
+            y = torch.randn(n, n, device="cuda", dtype=dt)
+            for _ in range(3):
+                torch.matmul(x, y)
+            best = 1e30
+            for _ in range(a.repeat):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(x, y)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = {"n": n, "tflops": 2.0 * n ** 3 / best / 1e12}
+            del x, y
+        torch.backends.cuda.matmul.allow_tf32 = False
+        out["device"] = torch.cuda.get_device_name()
+        print(json.dumps(out))
+        return 0
     prec = {"split": H.SPLIT_BF16, "fast": H.SPLIT_BF16_FAST, "fp64": H.FP64}[a.prec]
     ctx = H.Context(stream=torch.cuda.current_stream().cuda_stream)
     if a.cmd == "run":
         p = H.params(a.beta, a.delta, a.n_max, a.d_cut, a.steps, h=a.h, h1=a.h1, prec=prec,
-                     block_sparse=a.block_sparse if prec != H.FP64 else 0)
+                     block_sparse=a.block_sparse)
+        if a.profile:
+            H.hotrg_profile_enable(ctx.handle, True)
         t0 = time.perf_counter()
         res = ctx.run([p])[0]
         dt = time.perf_counter() - t0
-        print(json.dumps({"lnz_per_site": res.lnz_per_site, "seconds": dt,
-                          "ln_c": [res.step[k].ln_c for k in range(a.steps)],
-                          "side": [res.step[k].side for k in range(a.steps)]}))
+        out = {"lnz_per_site": res.lnz_per_site, "seconds": dt,
+               "ln_c": [res.step[k].ln_c for k in range(a.steps)],
+               "side": [res.step[k].side for k in range(a.steps)]}
+        if a.profile:
+            pr = H.hotrg_profile_read(ctx.handle)
+            out["profile"] = {f: (list(getattr(pr, f)) if hasattr(getattr(pr, f), "__len__") else getattr(pr, f))
+                              for f, _ in H.Profile._fields_}
+        print(json.dumps(out))
     elif a.cmd == "grid":
         import os
+
+        import numpy as np
         from . import replicas
         from .workloads import grid_points
         allp = grid_points()
@@ -129,7 +172,7 @@ def main(argv=None):
             dist.init_process_group("gloo")
         mine = replicas.shard(everything, world, rank)
         sel = [everything[i] for i in mine]
-        bs = a.block_sparse if prec != H.FP64 else 0
+        bs = a.block_sparse
         plist = [H.params(p.beta, p.delta, p.n_max, p.d_cut, p.n_steps, prec=prec, block_sparse=bs) for p in sel]
         tuned = None
         if a.nstreams == 0:
@@ -138,7 +181,7 @@ def main(argv=None):
         ctx.run_batch(plist[:4], nstreams=a.nstreams)  # workspaces and graphs of the classes
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = ctx.run_batch(plist, nstreams=a.nstreams)
+        res = H.hotrg_run_batch(ctx.handle, plist, nstreams=a.nstreams, check=False)  # failures stay per point
         dt = time.perf_counter() - t0
         counts = {}
         for p in sel:
@@ -151,15 +194,31 @@ def main(argv=None):
             dt = max(t)
             dist.destroy_process_group()
         if rank == 0:
-            print(json.dumps({"points": len(merged), "ranks": world, "seconds": dt,
-                              "points_per_s": len(merged) / dt, "d_cut_counts_rank0": counts, "autotune": tuned,
-                              "status": sorted(set(v[1] for v in merged.values()))}))
+            summary = {"points": len(merged), "ranks": world, "seconds": dt, "points_per_s": len(merged) / dt,
+                       "d_cut_counts_rank0": counts, "autotune": tuned,
+                       "status": sorted(set(v[1] for v in merged.values())),
+                       "failed": sum(1 for v in merged.values() if v[1] != 0)}
+            if a.check > 0 and world == 1:
+                idx = [int(i) for i in np.linspace(0, len(sel) - 1, a.check)]
+                chk = [H.params(sel[i].beta, sel[i].delta, sel[i].n_max, sel[i].d_cut, sel[i].n_steps,
+                                prec=H.FP64, block_sparse=1) for i in idx]
+                rf = ctx.run_batch(chk, nstreams=max(1, a.nstreams))
+                dl = [res[i].lnz_per_site - r.lnz_per_site for i, r in zip(idx, rf)]
+                summary["check_vs_fp64_block"] = {"points": len(idx), "max_abs_dlnz": max(abs(x) for x in dl),
+                                                  "d_cut": [sel[i].d_cut for i in idx],
+                                                  "dlnz": [float("%.3g" % x) for x in dl]}
+            if a.out:
+                with open(a.out, "w") as f:
+                    json.dump([{"beta": everything[i].beta, "delta": everything[i].delta,
+                                "d_cut": everything[i].d_cut, "lnz_per_site": v[0], "status": v[1]}
+                               for i, v in sorted(merged.items())], f)
+            print(json.dumps(summary))
     elif a.cmd == "surrogate":
         import numpy as np
         out = {}
 
         def mk(b, d):
-            return H.params(b, d, a.n_max, a.d_cut, a.steps, prec=prec, block_sparse=1 if prec != H.FP64 else 0)
+            return H.params(b, d, a.n_max, a.d_cut, a.steps, prec=prec, block_sparse=1)
 
         betas, deltas = np.linspace(0.6, 1.6, a.nb), np.linspace(0.1, 0.9, a.nd)
         X = np.array([[b, d] for d in deltas for b in betas])
@@ -195,8 +254,7 @@ def main(argv=None):
         temps = np.linspace(a.t_lo, a.t_hi, a.n_t)
         hbars = [float(v) for v in a.hbar.split(",") if v]
         field = {"auto": 0, "h": H.T_IMP_M, "h1": H.T_IMP_M1}[a.field]
-        base = H.params(1.0, a.delta, a.n_max, a.d_cut, a.steps, prec=prec,
-                        block_sparse=1 if prec != H.FP64 else 0)
+        base = H.params(1.0, a.delta, a.n_max, a.d_cut, a.steps, prec=prec, block_sparse=1)
         t0 = time.perf_counter()
         res = ctx.phase_scan(base, temps, hbars, field=field, dh=a.dh, nstreams=a.nstreams,
                              min_prominence=a.chi_prominence, check=False)

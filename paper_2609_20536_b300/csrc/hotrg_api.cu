@@ -21,6 +21,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
@@ -28,6 +31,13 @@
 namespace hotrg {
 
 std::atomic<long long> g_launches{0};
+
+bool attr_once(const void* kernel, int device) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    return done.insert({kernel, device}).second;
+}
 
 hotrg_status set_err(hotrg_ctx* ctx, hotrg_status st, const std::string& msg) {
     if (ctx) ctx->last_error = msg;
@@ -69,17 +79,21 @@ void prof_end(hotrg_ctx* ctx, int handle, int cls, double flops) {
 // Device-side flop counter of the block planner (its group sizes live on the device).
 hotrg_status prof_ensure_dflops(hotrg_ctx* ctx) {
     if (ctx->prof.dflops) return HOTRG_OK;
-    HOTRG_CUDA_TRY(ctx, cudaMalloc(&ctx->prof.dflops, 64));
-    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->prof.dflops, 0, 64, ctx->stream));
+    HOTRG_CUDA_TRY(ctx, cudaMalloc(&ctx->prof.dflops, 128));
+    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->prof.dflops, 0, 128, ctx->stream));
     return HOTRG_OK;
 }
 
 hotrg_status prof_fold(hotrg_ctx* ctx) {
     Profiler& P = ctx->prof;
     if (P.on && P.dflops) {  // called after a stream synchronisation: the counter is final
-        double h[3] = {0.0, 0.0, 0.0};
+        double h[9] = {0.0};
         if (cudaMemcpy(h, P.dflops, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
-            for (int c = 0; c < 3; ++c) P.tot.gemm_flops[c] += h[c];
+            for (int c = 0; c < 3; ++c) {
+                P.tot.gemm_flops[c] += h[c];
+                P.tot.operand_elems[c] += h[3 + c];
+                P.tot.output_elems[c] += h[6 + c];
+            }
             cudaMemsetAsync(P.dflops, 0, sizeof(h), ctx->stream);
             cudaStreamSynchronize(ctx->stream);
         }
@@ -169,9 +183,10 @@ static hotrg_status check_params(hotrg_ctx* ctx, const hotrg_params* p) {
         return set_err(ctx, HOTRG_ENOTSUP, "tensor-core forms need an sm_103 device");
     if (p->block_sparse < 0 || p->block_sparse > 1)
         return set_err(ctx, HOTRG_EINVAL, "block_sparse must be 0 or 1");
+    if (p->eig_mode < 0 || p->eig_mode > 1) return set_err(ctx, HOTRG_EINVAL, "eig_mode must be 0 or 1");
+    if (p->eig_fp64_iters < -1 || p->eig_fp64_iters > 8)
+        return set_err(ctx, HOTRG_EINVAL, "eig_fp64_iters must lie in [-1, 8]");
     if (p->gxy_q < 0 || p->gxy_q > 4) return set_err(ctx, HOTRG_EINVAL, "gxy_q must lie in [0, 4] (0: q = 2)");
-    if (p->block_sparse && p->prec == HOTRG_FP64)
-        return set_err(ctx, HOTRG_EINVAL, "block_sparse needs a split precision form");
     return HOTRG_OK;
 }
 
@@ -200,7 +215,7 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
     size_t g = 0;
     // the dense engine is needed unless every product of the step runs per block (the same
     // condition as do_step's)
-    const bool blocks = p->block_sparse && p->prec != HOTRG_FP64 && !imp && sym_of(p) != SYM_NONE;
+    const bool blocks = p->block_sparse && !imp && sym_of(p) != SYM_NONE;
     if (!blocks)
         for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
     if (blocks) {
@@ -212,7 +227,8 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
                                   {(int64_t)n, (int64_t)Dv * Dv, (int64_t)n}};
         for (auto& sh : gs)
             g = std::max(g, bs_plan_bytes(sh[0], sh[1], sh[2]) +
-                                umma_grouped_workspace(sh[0], sh[1], sh[2], sym_of(p)) + 4096);
+                                (p->prec == HOTRG_FP64 ? 0 : umma_grouped_workspace(sh[0], sh[1], sh[2], sym_of(p))) +
+                                4096);
     }
     b += g;
     return b;
@@ -274,7 +290,7 @@ static hotrg_status environment(hotrg_ctx* ctx, int prec, const double* T, int D
 }
 
 // T_out[u][d][x][x'] = sum P[l1,l2,x] T_up[l1,r1,u,i] T_dn[l2,r2,i,d] P[r1,r2,x']
-// Block-sparse environment (split forms, U(1) or Z2 labels).  The same three
+// Block-sparse environment (every precision form, U(1) or Z2 labels).  The same three
 // products as environment(), read straight out of T and written straight into
 // A2[a][a'][i][j], B2[a][a'][i][j] and E[a1][a2][a1'][a2'] through offset
 // tables (no permutation).  a is the truncated horizontal leg, b the other
@@ -295,8 +311,8 @@ static hotrg_status environment_blocks(hotrg_ctx* ctx, int prec, int sym, const 
     auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const double* X, const double* Y, double* C) {
         const size_t mark = ctx->ws.used;
         BsPlan pl;
-        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_ENV, pl);
-        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, X, 0, Y, 0, C, 0, PROF_GEMM_ENV);
+        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_ENV, pl, prec == HOTRG_FP64 ? INT32_MAX : 0);
+        if (st == HOTRG_OK) st = grouped_engine(ctx, prec, pl, X, 0, Y, 0, C, 0, PROF_GEMM_ENV);
         ctx->ws.used = mark;
         return st;
     };
@@ -394,8 +410,8 @@ static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, in
 }
 
 // One step; lnz_acc (device, may be null) += weight * ln c_k.
-// Block-sparse coarse contraction (split forms, pure runs with U(1) or Z2
-// labels).  Same s1 -> s2 -> s3 as coarse(), each contraction split into the
+// Block-sparse coarse contraction (pure runs with U(1) or Z2 labels; every
+// precision form).  Same s1 -> s2 -> s3 as coarse(), each contraction split into the
 // charge blocks of its index sets (q: labels of the legs, qh horizontal, qv
 // vertical, qn the new bond from the truncation):
 //   s1  M = (x, l2): q_x - q_l2     K = l1: q_l1           N = (r1, u, i): q_r1 - q_u + q_i
@@ -410,14 +426,16 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
                                   const double* T_dn, double* W, double* Z, double* Tc, double* T_out) {
     const int64_t h = Dh, v = Dv, p = Dp, hh = h * h, vv = v * v;
     hotrg_status s;
-    // W and Z are written and read as exact FP32 pairs (8 bytes, the value hi + lo): the
-    // tensor-core epilogue then needs no FP64 arithmetic for these two largest outputs
+    // In the split forms W and Z are written and read as exact FP32 pairs (8 bytes, the value
+    // hi + lo): the tensor-core epilogue then needs no FP64 arithmetic for these two largest
+    // outputs.  The FP64 form keeps them in FP64.
+    const int wf = prec == HOTRG_FP64 ? 0 : 1;
     auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const void* A, int af, const void* B,
                    void* C, int cf) {
         const size_t mark = ctx->ws.used;
         BsPlan pl;
-        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl);
-        if (st == HOTRG_OK) st = umma_grouped(ctx, prec, pl, A, af, B, 0, C, cf, PROF_GEMM_COARSE);
+        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl, prec == HOTRG_FP64 ? INT32_MAX : 0);
+        if (st == HOTRG_OK) st = grouped_engine(ctx, prec, pl, A, af, B, 0, C, cf, PROF_GEMM_COARSE);
         ctx->ws.used = mark;
         return st;
     };
@@ -429,7 +447,7 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
         BsSet M{2, {{qn, p, +1, 1, hh * vv}, {qh, h, -1, p, v}}, p * h};
         BsSet K{1, {{qh, h, +1, h * p, h * vv}}, h};
         BsSet N{3, {{qh, h, +1, vv, v * h * v}, {qv, v, -1, v, h * v}, {qv, v, +1, 1, 1}}, h * vv};
-        if ((s = run(M, K, N, P, 0, T_up, W, 1)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, P, 0, T_up, W, wf)) != HOTRG_OK) return s;
     }
     // s2: Z[x][u][d][r1][r2] = sum_{l2,i} W[x][r1][u][l2][i] T_dn[l2][r2][i][d]
     {
@@ -437,7 +455,7 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
                 p * h * v};
         BsSet K{2, {{qh, h, +1, v, h * vv}, {qv, v, +1, 1, v}}, h * v};
         BsSet N{2, {{qv, v, +1, 1, hh}, {qh, h, +1, vv, 1}}, v * h};
-        if ((s = run(M, K, N, W, 1, T_dn, Z, 1)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, W, wf, T_dn, Z, wf)) != HOTRG_OK) return s;
     }
     // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][u][d][r1][r2] P[r1][r2][x']
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(Tc, 0, (size_t)p * vv * p * 8, ctx->stream));
@@ -445,7 +463,7 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
         BsSet M{3, {{qn, p, +1, vv * hh, vv * p}, {qv, v, +1, v * hh, v * p}, {qv, v, -1, hh, p}}, p * vv};
         BsSet K{2, {{qh, h, +1, h, h * p}, {qh, h, +1, 1, p}}, hh};
         BsSet N{1, {{qn, p, +1, 1, 1}}, p};
-        if ((s = run(M, K, N, Z, 1, P, Tc, 0)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, Z, wf, P, Tc, 0)) != HOTRG_OK) return s;
     }
     // relabel for the other axis: T_out[u][d][x][x'] = Tc[x][u][d][x']
     Perm po{4, {Dv, Dv, Dp, Dp}, {(int64_t)Dv * Dp, Dp, vv * Dp, 1}};
@@ -493,7 +511,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     hotrg_status s;
     const int h_step = prof_begin(ctx);
     const int sym = sym_of(p);
-    const bool blocks = p->block_sparse && prec != HOTRG_FP64 && !Ti_in && sym != SYM_NONE;
+    const bool blocks = p->block_sparse && !Ti_in && sym != SYM_NONE;
     if (blocks) {
         if ((s = environment_blocks(ctx, prec, sym, T_in, q_h, q_v, Dh, Dv, false, A2, B2, EL)) != HOTRG_OK)
             return s;
@@ -517,7 +535,11 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     plan.tie_rtol = p->tie_rtol > 0 ? p->tie_rtol : 1e-9;
     plan.side_rtol = p->side_rtol > 0 ? p->side_rtol : 1e-6;
     plan.env_policy = p->env_policy;
-    plan.exact = prec == HOTRG_FP64;
+    // the FP64 form lists the large U(1) blocks by subspace iteration refined in FP64 (U(1) blocks
+    // list at least twice the states they keep, so the iteration converges fast); with Z2 or no
+    // symmetry it solves every block by Jacobi; eig_mode = 1 asks for Jacobi everywhere
+    plan.exact = p->eig_mode == 1 || (prec == HOTRG_FP64 && plan.sym != SYM_U1);
+    plan.fp64_iters = p->eig_fp64_iters > 0 ? p->eig_fp64_iters : (p->eig_fp64_iters < 0 ? 0 : (prec == HOTRG_FP64 ? 3 : 0));
     const int h_eig = prof_begin(ctx);
     if ((s = eig_truncate(ctx, plan, EL, p->env_policy == 0 ? ER : nullptr, q_h, P, q_out, info, eigws)) !=
         HOTRG_OK)
@@ -547,6 +569,16 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     return HOTRG_OK;
 }
 
+// hotrg_step: an engine failure of the step (its status word) goes into the step's info
+// unless the eigensolver already reported one; the word is cleared for the next step.
+__global__ void fold_status_kernel(hotrg_step_info* info, int32_t* st) {
+    if (threadIdx.x == 0) {
+        const int32_t e = *st;
+        if (e != 0 && info && info->status == 0) info->status = e;
+        *st = 0;
+    }
+}
+
 __global__ void log_kernel(double* dst, const double* src) {
     if (threadIdx.x == 0) *dst = log(*src);
 }
@@ -563,6 +595,14 @@ __global__ void finish_kernel(double* lnz_acc, const double* tr, double weight, 
 
 struct RunDev {
     double lnz, ln_c0, ln_tr, imp_ratio, tr, tr_imp, norm0;
+    int32_t status, pad;  // the engine's status word while this point runs (zeroed with the block)
+};
+
+// While a point is enqueued (or captured) the engine reports into the point's own slot.
+struct StatusSlot {
+    hotrg_ctx* ctx;
+    StatusSlot(hotrg_ctx* c, int32_t* slot) : ctx(c) { ctx->status_slot = slot; }
+    ~StatusSlot() { ctx->status_slot = nullptr; }
 };
 
 // Buffers and sizes of one point; carved deterministically from the workspace
@@ -635,6 +675,7 @@ static hotrg_status plan_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_ki
 // pl.dparams: no host synchronisation and no allocation, so it can be captured.
 static hotrg_status enqueue_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kind, PointPlan& pl) {
     cudaStream_t st = ctx->stream;
+    StatusSlot slot(ctx, &pl.rd->status);
     const int D0 = pl.D0;
     const bool imp = pl.imp;
     hotrg_status s;
@@ -695,6 +736,14 @@ static hotrg_status unpack_point(hotrg_ctx* ctx, const hotrg_params* p, const Po
     out->imp_ratio = pl.imp ? h.imp_ratio : 0.0;
     out->n_steps = p->n_steps;
     out->status = HOTRG_OK;
+    if (h.status != 0) {
+        out->status = h.status;
+        return set_err(ctx, (hotrg_status)h.status,
+                       h.status == HOTRG_ENOTSUP
+                           ? "block planner: a product's label sums span more values than its table, or a charge "
+                             "block is wider than the slice pitch"
+                           : "tensor-core engine: a bounded wait ran out");
+    }
     for (int k = 0; k < p->n_steps; ++k)
         if (out->step[k].status != HOTRG_OK) {
             out->status = out->step[k].status;
@@ -728,11 +777,6 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
                                         cudaMemcpyDeviceToHost, st));
     HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     prof_fold(ctx);
-    if (p->prec != HOTRG_FP64)
-        if ((s = umma_check_status(ctx)) != HOTRG_OK) {
-            out->status = s;
-            return s;
-        }
     return unpack_point(ctx, p, pl, h, out);
 }
 
@@ -740,7 +784,8 @@ static hotrg_status run_point(hotrg_ctx* ctx, const hotrg_params* p, int imp_kin
 // Batched points: LPT over worker streams, one CUDA graph per point class.
 // ---------------------------------------------------------------------------
 struct ClassKey {
-    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z, block_sparse, q;
+    int n_max, d_cut, n_steps, prec, env_policy, tkind, m_range, eig_max_sweeps, imp_kind, hz, h1z, block_sparse, q,
+        eig_mode, eig_fp64_iters;
     double tie_rtol, eig_tol;
     bool operator==(const ClassKey& o) const { return memcmp(this, &o, sizeof(ClassKey)) == 0; }
 };
@@ -761,6 +806,8 @@ static ClassKey class_of(const hotrg_params* p, int imp_kind) {
     k.h1z = p->h1 == 0.0;
     k.block_sparse = p->block_sparse;
     k.q = p->gxy_q == 0 ? 2 : p->gxy_q;
+    k.eig_mode = p->eig_mode;
+    k.eig_fp64_iters = p->eig_fp64_iters;
     k.tie_rtol = p->tie_rtol;
     k.eig_tol = p->eig_tol;
     return k;
@@ -801,6 +848,8 @@ static void profile_add(hotrg_profile& a, const hotrg_profile& b) {
         a.gemm_calls[c] += b.gemm_calls[c];
         a.gemm_ms[c] += b.gemm_ms[c];
         a.gemm_flops[c] += b.gemm_flops[c];
+        a.operand_elems[c] += b.operand_elems[c];
+        a.output_elems[c] += b.output_elems[c];
     }
     a.slice_ms += b.slice_ms;
     a.eig_ms += b.eig_ms;
@@ -818,6 +867,7 @@ static void batch_free(Batch* b) {
             if (w.ctx->ws.base) cudaFree(w.ctx->ws.base);
             for (cudaEvent_t e : w.ctx->prof.pool) cudaEventDestroy(e);
             if (w.ctx->prof.dflops) cudaFree(w.ctx->prof.dflops);
+            if (w.ctx->status_dev) cudaFree(w.ctx->status_dev);
             delete w.ctx;
         }
         if (w.done) cudaEventDestroy(w.done);
@@ -856,9 +906,16 @@ hotrg_status hotrg_create(hotrg_ctx** out, size_t workspace_bytes, void* cuda_st
     ctx->sm_count = prop.multiProcessorCount;
     ctx->smem_optin = (int)prop.sharedMemPerBlockOptin;
     ctx->tc_ok = prop.major == 10 && prop.minor == 3;
+    if (cudaMalloc(&ctx->status_dev, 64) != cudaSuccess || cudaMemset(ctx->status_dev, 0, 64) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->status_dev) cudaFree(ctx->status_dev);
+        delete ctx;
+        return HOTRG_ENOMEM;
+    }
     if (workspace_bytes) {
         hotrg_status s = ws_reserve(ctx, workspace_bytes);
         if (s != HOTRG_OK) {
+            cudaFree(ctx->status_dev);
             delete ctx;
             return s;
         }
@@ -878,6 +935,7 @@ void hotrg_destroy(hotrg_ctx* ctx) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(ctx->ws.base);
     }
+    if (ctx->status_dev) cudaFree(ctx->status_dev);
     delete ctx;
 }
 
@@ -893,7 +951,7 @@ hotrg_status hotrg_profile_enable(hotrg_ctx* ctx, int32_t enable) {
     if (ctx->prof.on) {
         hotrg_status s = prof_ensure_dflops(ctx);
         if (s != HOTRG_OK) return s;
-        HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->prof.dflops, 0, 64, ctx->stream));
+        HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(ctx->prof.dflops, 0, 128, ctx->stream));
         HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     }
     memset(&ctx->prof.tot, 0, sizeof(ctx->prof.tot));
@@ -951,6 +1009,11 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, const hotrg_params* p, const double* T_i
     int dp = 0;
     s = do_step(ctx, p, T_in, q_h, q_v, Dh, Dv, T_out, q_out, &dp, info_dev, T_imp_in, T_imp_out, nullptr, 0.0);
     *dprime = dp;
+    if (s == HOTRG_OK) {
+        fold_status_kernel<<<1, 32, 0, ctx->stream>>>(info_dev, ctx->status_dev);
+        HOTRG_COUNT(1);
+        HOTRG_LAUNCH_CHECK(ctx, "fold_status_kernel");
+    }
     return s;
 }
 
@@ -1032,6 +1095,8 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
             wk.ctx->sm_count = ctx->sm_count;
             wk.ctx->smem_optin = ctx->smem_optin;
             wk.ctx->tc_ok = ctx->tc_ok;
+            HOTRG_CUDA_TRY(ctx, cudaMalloc(&wk.ctx->status_dev, 64));
+            HOTRG_CUDA_TRY(ctx, cudaMemset(wk.ctx->status_dev, 0, 64));
             HOTRG_CUDA_TRY(ctx, cudaEventCreateWithFlags(&wk.done, cudaEventDisableTiming));
             B->workers.push_back(wk);
         }
@@ -1175,10 +1240,6 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
             profile_add(ctx->prof.tot, w.ctx->prof.tot);
             memset(&w.ctx->prof.tot, 0, sizeof(w.ctx->prof.tot));
         }
-    if (err == HOTRG_OK) {
-        hotrg_status us = umma_check_status(ctx);
-        if (us != HOTRG_OK) err = us;
-    }
     for (int i : valid) {
         if (err != HOTRG_OK) {
             out[i].status = err;

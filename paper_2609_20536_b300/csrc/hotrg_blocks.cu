@@ -8,7 +8,7 @@
 // each element of M, K and N carries a value v (a signed sum of its legs'
 // labels) and A[m, k] B[n, k] can be nonzero only when v(m) = v(k) = v(n).
 // The planner sorts each index set by v (a deterministic counting sort: one
-// warp per 256-element chunk, ranks from warp vote masks, no atomics on the
+// warp per 1024-element chunk, ranks from warp vote masks, no atomics on the
 // order), and lays out one group per value present in both M and N:
 //   rows of the group  -> positions mbase .. mbase + M_g - 1 of the sorted M list
 //   padded slice rows  -> mpad .. mpad + round_up(M_g, 128) - 1
@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(32 * 9) bs_centre_kernel(BsSet M, BsSet K, BsS
     }
 }
 
-// counts[chunk][BS_V]: elements of each value in every BS_CHUNK-element chunk.
+// counts[value][chunk]: elements of each value in every BS_CHUNK-element chunk (value-major,
+// so that the single-block scan reads each value's counts contiguously).
 __global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sym, int32_t* __restrict__ counts,
                                                                  int64_t nchunks, const int32_t* __restrict__ centre,
                                                                  int32_t* status) {
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sy
         if (ok && (__ffs(m) - 1) == lane) tab[w][v] += __popc(m);
         __syncwarp();
     }
-    for (int v = lane; v < BS_V; v += 32) counts[chunk * BS_V + v] = tab[w][v];
+    for (int v = lane; v < BS_V; v += 32) counts[(int64_t)v * nchunks + chunk] = tab[w][v];
 }
 
 // One block of 1024 threads (32 warps): per-value totals and bases, per-chunk
@@ -142,8 +143,8 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
                                                        const int32_t* __restrict__ cN, int64_t nN,
                                                        int32_t* __restrict__ sM, int32_t* __restrict__ sK,
                                                        int32_t* __restrict__ sN, BsGroup* __restrict__ groups,
-                                                       BsHeader* __restrict__ hdr, double* flops_acc, int kp_cap,
-                                                       int32_t* status) {
+                                                       BsHeader* __restrict__ hdr, double* prof_acc, int prof_class,
+                                                       int kp_cap, int32_t* status) {
     __shared__ int64_t tot[3][BS_V], base[3][BS_V];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int v = threadIdx.x;  // thread 0 below builds the group table
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
     for (int s = 0; s < 3; ++s)
         for (int u = warp; u < BS_V; u += nw) {
             int64_t t = 0;
-            for (int64_t c = lane; c < ns[s]; c += 32) t += cs[s][c * BS_V + u];
+            for (int64_t c = lane; c < ns[s]; c += 32) t += cs[s][(int64_t)u * ns[s] + c];
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) tot[s][u] = t;
         }
@@ -172,20 +173,20 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
             int64_t run = base[s][u];
             for (int64_t c0 = 0; c0 < ns[s]; c0 += 32) {
                 const int64_t c = c0 + lane;
-                const int32_t x = c < ns[s] ? cs[s][c * BS_V + u] : 0;
+                const int32_t x = c < ns[s] ? cs[s][(int64_t)u * ns[s] + c] : 0;
                 int32_t inc = x;  // inclusive scan over the 32 chunks
                 for (int o = 1; o < 32; o <<= 1) {
                     const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
                     if (lane >= o) inc += y;
                 }
-                if (c < ns[s]) ss[s][c * BS_V + u] = (int32_t)(run + inc - x);
+                if (c < ns[s]) ss[s][(int64_t)u * ns[s] + c] = (int32_t)(run + inc - x);
                 run += __shfl_sync(0xffffffffu, inc, 31);
             }
         }
     if (v == 0) {
         int G = 0;
         int64_t mpad = 0, npad = 0, tiles = 0;
-        double fl = 0.0;
+        double fl = 0.0, opnd = 0.0, outp = 0.0;
         for (int u = 0; u < BS_V; ++u) {
             if (tot[0][u] == 0 || tot[2][u] == 0) continue;
             BsGroup g;
@@ -209,6 +210,8 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
             npad += (g.N + 127) / 128 * 128;
             tiles += (int64_t)((g.M + 127) / 128) * g.tiles_n;
             fl += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+            opnd += ((double)g.M + (double)g.N) * (double)g.K;
+            outp += (double)g.M * (double)g.N;
             groups[G++] = g;
         }
         hdr->G = G;
@@ -216,7 +219,11 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
         hdr->mpad_total = mpad;
         hdr->npad_total = npad;
         hdr->flops = fl;
-        if (flops_acc) *flops_acc += fl;
+        if (prof_acc) {
+            prof_acc[prof_class] += fl;
+            prof_acc[3 + prof_class] += opnd;
+            prof_acc[6 + prof_class] += outp;
+        }
     }
 }
 
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(32 * BS_WARPS) bs_place_kernel(BsSet S, int sy
     const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
     if (chunk >= nchunks) return;
     const int shift = BS_VOFF - *centre;
-    for (int v = lane; v < BS_V; v += 32) tab[w][v] = starts[chunk * BS_V + v];
+    for (int v = lane; v < BS_V; v += 32) tab[w][v] = starts[(int64_t)v * nchunks + chunk];
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
     const int64_t lo = chunk * BS_CHUNK, hi = min(lo + BS_CHUNK, S.size);
@@ -266,7 +273,7 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN) {
 }
 
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
-                     BsPlan& out) {
+                     BsPlan& out, int32_t kp_cap_override) {
     const BsSet* sets[3] = {&M, &K, &N};
     int32_t* counts[3];
     int32_t* starts[3];
@@ -293,12 +300,12 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
         bs_count_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, counts[i], nch[i], centre, st);
     }
-    double* facc = (ctx->prof.on && ctx->prof.dflops) ? ctx->prof.dflops + prof_class : nullptr;
+    double* facc = (ctx->prof.on && ctx->prof.dflops && prof_class >= 0 && prof_class < 3) ? ctx->prof.dflops : nullptr;
     // slice pitch: the whole K set for small sets and Z2 (two blocks); half of it for larger U(1)
     // sets, whose blocks hold a small fraction of K (the device checks every block against it)
-    out.kp_cap = bs_pitch(K.size, sym);
+    out.kp_cap = kp_cap_override > 0 ? kp_cap_override : bs_pitch(K.size, sym);
     bs_scan_kernel<<<1, BS_SCAN_THREADS, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
-                                      starts[2], out.groups, out.hdr, facc, out.kp_cap, st);
+                                      starts[2], out.groups, out.hdr, facc, prof_class, out.kp_cap, st);
     for (int i = 0; i < 3; ++i) {
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
         bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], centre, offs[i][0],

@@ -1002,6 +1002,10 @@ __global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, 
         }
         __syncthreads();
         const int sw = jacobi_block(H, W, b, max_sweeps, tol, rc, rs, rp, rq, red, &s_rot);
+        // W (b x b) is kept for a further FP64 iteration (rr_next_kernel): the FP32 basis that
+        // S1 held has been consumed by rr_prep_kernel
+        double* Wg = w.S1[side] + aoff;
+        for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) Wg[idx] = W[idx];
         // Ritz vectors V = Q W (m x b)
         double* V = w.V[side] + aoff;
         for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) {
@@ -1023,6 +1027,93 @@ __global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, 
                 atomicExch(w.status, (int)HOTRG_ENOCONV);
             else
                 atomicMax(&w.sweeps[side], sw);
+        }
+        __syncthreads();
+    }
+}
+
+// One more FP64 subspace iteration after a Rayleigh-Ritz step: the Ritz basis
+// V = Q W has E_q V = Y W (Y = E_q Q from rr_product_kernel, W from
+// rr_finish_kernel), so the next basis is the orthonormalised Z = Y W.  Its
+// columns are E_q v_j ~ theta_j v_j, nearly orthogonal once normalised, so one
+// Cholesky QR (as in rr_prep_kernel, dropping columns whose pivot falls below
+// 1e-8 of their unit norm) orthonormalises them to rounding.  Each such
+// iteration shrinks the error of the j-th Ritz vector by lambda_{b+1} /
+// lambda_j.  Result in S2 (m x b row-major), ready for rr_product_kernel.
+__global__ void __launch_bounds__(SUB_THREADS) rr_next_kernel(EigWs w) {
+    extern __shared__ double G[];  // bcap x bcap (the Gram matrix), then bcap x bcap (W)
+    __shared__ int live[BCAP_MAX];
+    __shared__ double cn[BCAP_MAX];
+    const int side = blockIdx.y;
+    const int nsec = *w.nsec;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int sct = blockIdx.x; sct < nsec; sct += gridDim.x) {
+        const int m = w.sec_start[sct + 1] - w.sec_start[sct];
+        const int b = w.sec_b[sct];
+        if (b == m) continue;
+        const int64_t aoff = w.sec_aoff[sct];
+        const double* Y = w.S4[side] + aoff;
+        double* Z = w.S2[side] + aoff;
+        double* Ws = G + b * b;
+        for (int idx = tid; idx < b * b; idx += blockDim.x) Ws[idx] = w.S1[side][aoff + idx];
+        __syncthreads();
+        for (int64_t idx = tid; idx < (int64_t)m * b; idx += blockDim.x) {
+            const int t = (int)(idx / b), j = (int)(idx % b);
+            double a = 0.0;
+            for (int i = 0; i < b; ++i) a = fma(Y[(int64_t)t * b + i], Ws[i * b + j], a);
+            Z[idx] = a;
+        }
+        __syncthreads();
+        // unit column norms (a zero column stays zero and is dropped below)
+        for (int j = warp; j < b; j += nw) {
+            double a = 0.0;
+            for (int t = lane; t < m; t += 32) a = fma(Z[(int64_t)t * b + j], Z[(int64_t)t * b + j], a);
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) cn[j] = a > 1e-280 ? 1.0 / sqrt(a) : 0.0;
+        }
+        __syncthreads();
+        for (int64_t idx = tid; idx < (int64_t)m * b; idx += blockDim.x) Z[idx] *= cn[(int)(idx % b)];
+        __syncthreads();
+        for (int task = warp; task < b * b; task += nw) {
+            const int i = task / b, j = task % b;
+            if (i > j) continue;
+            double a = 0.0;
+            for (int t = lane; t < m; t += 32) a = fma(Z[(int64_t)t * b + i], Z[(int64_t)t * b + j], a);
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) {
+                G[i * b + j] = a;
+                G[j * b + i] = a;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int j = 0; j < b; ++j) {
+                const double d = G[j * b + j];
+                __syncwarp();
+                const bool ok = d > 1e-8;
+                if (lane == 0) live[j] = ok ? 1 : 0;
+                const double rjj = ok ? sqrt(d) : 1.0;
+                for (int c = j + lane; c < b; c += 32) G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] / rjj) : (c == j ? 1.0 : 0.0);
+                __syncwarp();
+                for (int idx = lane; idx < b * b; idx += 32) {
+                    const int r = idx / b, c = idx % b;
+                    if (r > j && c >= r) G[r * b + c] -= G[j * b + r] * G[j * b + c];
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int t = tid; t < m; t += blockDim.x) {
+            double* q = Z + (int64_t)t * b;
+            for (int j = 0; j < b; ++j) {
+                if (!live[j]) {
+                    q[j] = 0.0;
+                    continue;
+                }
+                double a = q[j];
+                for (int i = 0; i < j; ++i) a = fma(-q[i], G[i * b + j], a);
+                q[j] = a / G[j * b + j];
+            }
         }
         __syncthreads();
     }
@@ -1203,14 +1294,12 @@ __global__ void projector_kernel(int dprime, int policy, double side_rtol, EigWs
     }
 }
 
-static bool g_attr_done = false;
-
 hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL, const double* ER,
                           const int32_t* q_h, double* P, int32_t* q_out, hotrg_step_info* info, void* ws) {
     const int n = plan.n;
     if (n > MAX_N) return set_err(ctx, HOTRG_EINVAL, "eig_truncate: Dh^2 above 16384");
     cudaStream_t st = ctx->stream;
-    if (!g_attr_done) {
+    if (attr_once((const void*)sectors_kernel, ctx->device)) {
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(sectors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  MAX_N * 8));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(jacobi_sectors_kernel,
@@ -1223,7 +1312,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
                                                  SUBF_SMEM));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  BCAP_MAX * BCAP_MAX * (int)sizeof(double)));
-        g_attr_done = true;
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_next_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 2 * BCAP_MAX * BCAP_MAX * (int)sizeof(double)));
     }
     EigWs w = carve(ws, n);
     // listed width of large blocks in the split forms
@@ -1284,6 +1374,14 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         HOTRG_LAUNCH_CHECK(ctx, "rr_product_kernel");
         rr_finish_kernel<<<dim3(sgrid, sides), JAC_THREADS, RR_SMEM_BYTES, st>>>(plan.max_sweeps, plan.tol, w);
         HOTRG_LAUNCH_CHECK(ctx, "rr_finish_kernel");
+        // further FP64 subspace iterations, each followed by its Rayleigh-Ritz step
+        for (int r = 0; r < plan.fp64_iters; ++r) {
+            rr_next_kernel<<<dim3(sgrid, sides), SUB_THREADS, (size_t)2 * bcap * bcap * sizeof(double), st>>>(w);
+            rr_product_kernel<<<dim3(tiles < 64 ? tiles : 64, sgrid < 32 ? sgrid : 32, sides), 256, 0, st>>>(w);
+            rr_finish_kernel<<<dim3(sgrid, sides), JAC_THREADS, RR_SMEM_BYTES, st>>>(plan.max_sweeps, plan.tol, w);
+            HOTRG_COUNT(3);
+            HOTRG_LAUNCH_CHECK(ctx, "FP64 subspace iteration");
+        }
         prof_end(ctx, hp2, PROF_EIG_PART0 + 2, 0.0);
     }
     const int hp3 = prof_begin(ctx);

@@ -1,6 +1,8 @@
 // Contraction engine dispatch: every contraction of a step is C = A B^T with
-// K-contiguous FP64 operands and an FP64 result.  HOTRG_FP64 runs the SIMT
-// DFMA kernel; the tensor-core split forms live in hotrg_umma.cu.
+// K-contiguous FP64 operands and an FP64 result (dense), or a grouped product
+// over charge blocks (block-sparse).  HOTRG_FP64 runs the SIMT DFMA kernels
+// (dense: hotrg_kernels.cu, grouped: hotrg_grouped_f64.cu); the tensor-core
+// split forms live in hotrg_umma.cu.
 #include "internal.cuh"
 
 namespace hotrg {
@@ -24,6 +26,12 @@ hotrg_status gemm_engine(hotrg_ctx* ctx, int prec, int M, int N, int K, const do
     hotrg_status s = umma_gemm(ctx, prec, M, N, K, A, lda, B, ldb, C, ldc, coarse);
     ctx->ws.used = mark;
     return s;
+}
+
+hotrg_status grouped_engine(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void* A, int afmt, const void* B,
+                            int bfmt, void* C, int cfmt, int prof_class) {
+    if (prec == HOTRG_FP64) return dgemm_grouped(ctx, pl, A, afmt, B, bfmt, C, cfmt, prof_class);
+    return umma_grouped(ctx, prec, pl, A, afmt, B, bfmt, C, cfmt, prof_class);
 }
 
 size_t gemm_engine_workspace(int prec, int64_t M, int64_t N, int64_t K) {

@@ -658,12 +658,9 @@ template <int NS>
 static hotrg_status launch_umma(hotrg_ctx* ctx, const __nv_bfloat16* As, const __nv_bfloat16* Bs, int M, int N,
                                 int Kp, const UmmaArgs& a) {
     using Cfg = UmmaCfg<NS>;
-    static bool attr = false;
-    if (!attr) {
+    if (attr_once((const void*)umma_gemm_kernel<NS>, ctx->device))
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_gemm_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  Cfg::SMEM));
-        attr = true;
-    }
     CUtensorMap mA, mB;
     if (!make_map(&mA, As, NS, M, Kp, BM) || !make_map(&mB, Bs, NS, N, Kp, BN))
         return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
@@ -676,18 +673,9 @@ static hotrg_status launch_umma(hotrg_ctx* ctx, const __nv_bfloat16* As, const _
     return HOTRG_OK;
 }
 
-static int32_t* g_status = nullptr;  // per-process device status word of the engine
-
-int32_t* umma_status_word(hotrg_ctx* ctx) {
-    if (!g_status) {
-        if (cudaMalloc(&g_status, 64) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        cudaMemsetAsync(g_status, 0, 64, ctx->stream);
-    }
-    return g_status;
-}
+// The status word kernels enqueued through ctx report into: the slot of the point being
+// enqueued, else the context's own word (made with the context, on its device).
+int32_t* umma_status_word(hotrg_ctx* ctx) { return ctx->status_slot ? ctx->status_slot : ctx->status_dev; }
 
 hotrg_status umma_gemm_fmt(hotrg_ctx* ctx, int prec, int M, int N, int K, const void* A, int afmt, int64_t lda,
                            const void* B, int bfmt, int64_t ldb, void* C, int cfmt, int64_t ldc, bool coarse) {
@@ -766,15 +754,13 @@ hotrg_status umma_gemm_gather(hotrg_ctx* ctx, int prec, int M, int N, int K, con
     if (!As || !Bs || !eA || !eB) return set_err(ctx, HOTRG_ENOMEM, "umma workspace exhausted");
     int32_t* st = umma_status_word(ctx);
     if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
-    static bool attr = false;
-    if (!attr) {
+    if (attr_once((const void*)slice_gather_kernel<FMT_F64>, ctx->device)) {
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_gather_kernel<FMT_F64>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  GATHER_WARPS * GATHER_SMEM_K * 8));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_gather_kernel<FMT_F32PAIR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  GATHER_WARPS * GATHER_SMEM_K * 8));
-        attr = true;
     }
     cudaStream_t s = ctx->stream;
     const int smem = K <= GATHER_SMEM_K ? GATHER_WARPS * GATHER_SMEM_K * 8 : 0;
@@ -1238,12 +1224,9 @@ template <int NS, int OUT>
 static hotrg_status launch_grouped(hotrg_ctx* ctx, const __nv_bfloat16* As, int64_t rA, const __nv_bfloat16* Bs,
                                    int64_t rB, int Kp, const GroupArgs& a, int prof_class) {
     using Cfg = GroupCfg<NS>;
-    static bool attr = false;
-    if (!attr) {
+    if (attr_once((const void*)umma_grouped_kernel<NS, OUT>, ctx->device))
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS, OUT>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
-        attr = true;
-    }
     CUtensorMap mA, mB;
     if (!make_map(&mA, As, NS, rA, Kp, BM) || !make_map(&mB, Bs, NS, rB, Kp, BN))
         return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
@@ -1268,15 +1251,13 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
     if (!As || !Bs || !eA || !eB) return set_err(ctx, HOTRG_ENOMEM, "umma workspace exhausted");
     int32_t* st = umma_status_word(ctx);
     if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
-    static bool attr = false;
-    if (!attr) {
+    if (attr_once((const void*)slice_grouped_kernel<FMT_F64>, ctx->device)) {
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel<FMT_F64>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  GATHER_WARPS * GROUP_SMEM_K * 8));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(slice_grouped_kernel<FMT_F32PAIR>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  GATHER_WARPS * GROUP_SMEM_K * 8));
-        attr = true;
     }
     cudaStream_t s = ctx->stream;
     const int smem = GATHER_WARPS * GROUP_SMEM_K * 8;
@@ -1318,12 +1299,12 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
 }
 
 hotrg_status umma_check_status(hotrg_ctx* ctx) {
-    if (!g_status) return HOTRG_OK;
+    if (!ctx->status_dev) return HOTRG_OK;
     int32_t h = 0;
-    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, g_status, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    HOTRG_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctx->status_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
     HOTRG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     if (h != 0) {
-        cudaMemsetAsync(g_status, 0, 4, ctx->stream);
+        cudaMemsetAsync(ctx->status_dev, 0, 4, ctx->stream);
         return set_err(ctx, (hotrg_status)h,
                        h == HOTRG_ENOTSUP ? "block planner: a product's label sums span more values than its table, "
                                             "or a charge block is wider than the slice pitch"

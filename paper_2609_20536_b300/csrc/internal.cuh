@@ -28,7 +28,9 @@ struct ProfMark {
 
 struct Profiler {
     bool on = false;
-    double* dflops = nullptr;  // device: algorithmic flops counted by the block planner, per GEMM class
+    // device, 16 doubles: per GEMM class c the block planner adds the algorithmic flops at [c],
+    // the operand elements at [3 + c] and the output elements at [6 + c]
+    double* dflops = nullptr;
     std::vector<cudaEvent_t> pool;
     std::vector<ProfMark> pending;
     hotrg_profile tot{};
@@ -58,12 +60,22 @@ struct hotrg_ctx {
     hotrg::Profiler prof;
     void* batch = nullptr;  // worker streams and graph cache of hotrg_run_batch
     int tuned_streams = 0;  // hotrg_autotune_batch's choice (0: not tuned, batch calls default to 2)
+    // Engine status words (bounded waits that ran out, planner overflow): status_dev is this
+    // context's own (64 bytes on ctx->device, made with the context); while a point is enqueued
+    // status_slot points at that point's slot in its device result block, so that a failure is
+    // reported for that point alone (also inside captured graphs).
+    int32_t* status_dev = nullptr;
+    int32_t* status_slot = nullptr;
 };
 
 namespace hotrg {
 
 // ---- error helpers -------------------------------------------------------
 hotrg_status set_err(hotrg_ctx* ctx, hotrg_status st, const std::string& msg);
+
+// Kernel attributes (cudaFuncSetAttribute) belong to one device: true the first time
+// a (kernel, device) pair is seen, so that the caller sets them once per device.
+bool attr_once(const void* kernel, int device);
 
 #define HOTRG_CUDA_TRY(ctx, call)                                                           \
     do {                                                                                    \
@@ -129,7 +141,8 @@ struct EigPlan {
     double tie_rtol;
     double side_rtol;
     int env_policy;
-    bool exact;   // FP64 Jacobi on every block (the FP64 form)
+    bool exact;      // FP64 Jacobi on every block
+    int fp64_iters;  // FP64 subspace iterations after the first Rayleigh-Ritz step (subspace path)
 };
 size_t eig_workspace_bytes(int Dh);
 // E[0] = E_L, E[1] = E_R (E[1] may be null when env_policy == 1).  Writes P
@@ -157,7 +170,7 @@ int32_t* umma_status_word(hotrg_ctx* ctx);
 // ---- block-sparse contractions (hotrg_blocks.cu, hotrg_umma.cu) -----------
 constexpr int BS_V = 128;       // charge values tracked per index set
 constexpr int BS_VOFF = 64;     // value v is stored at slot v - centre + BS_VOFF (centre: bs_centre_kernel)
-constexpr int BS_CHUNK = 256;   // elements per warp in the counting passes
+constexpr int BS_CHUNK = 1024;  // elements per warp in the counting passes
 
 // One leg of an index set: its label array, extent, sign in the set's value,
 // and its element strides in the two tensors that use the set.
@@ -198,8 +211,9 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // symmetry; the value table (BS_V slots) is centred on the product's range of
 // label sums, and a product whose sums span BS_V or more values records
 // HOTRG_ENOTSUP in the engine's status word.
+// kp_cap_override > 0 replaces the slice pitch limit (the FP64 engine slices nothing).
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
-                     BsPlan& out);
+                     BsPlan& out, int32_t kp_cap_override = 0);
 // Slice row pitch of a grouped product: the whole K set rounded to 32 for small sets and
 // Z2; half of it (at least 4096) for larger U(1) sets (bs_plan checks every block on the device).
 int32_t bs_pitch(int64_t nK, int sym);
@@ -207,5 +221,11 @@ size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN, int sym);
 // Operand / output formats: 0 = FP64, 1 = exact FP32 pairs (hi, lo) with value hi + lo.
 hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void* A, int afmt, const void* B,
                           int bfmt, void* C, int cfmt, int prof_class);
+// The same grouped product in plain FP64 (SIMT FMA; FP64 operands and output only).
+hotrg_status dgemm_grouped(hotrg_ctx* ctx, const BsPlan& pl, const void* A, int afmt, const void* B, int bfmt,
+                           void* C, int cfmt, int prof_class);
+// Grouped product through the engine of the precision form.
+hotrg_status grouped_engine(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void* A, int afmt, const void* B,
+                            int bfmt, void* C, int cfmt, int prof_class);
 
 }  // namespace hotrg

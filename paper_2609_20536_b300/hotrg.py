@@ -36,6 +36,7 @@ class Params(ctypes.Structure):
         ("eig_max_sweeps", ctypes.c_int32), ("tkind", ctypes.c_int32),
         ("tie_rtol", ctypes.c_double), ("eig_tol", ctypes.c_double), ("side_rtol", ctypes.c_double),
         ("block_sparse", ctypes.c_int32), ("gxy_q", ctypes.c_int32),
+        ("eig_mode", ctypes.c_int32), ("eig_fp64_iters", ctypes.c_int32),
     ]
 
 
@@ -60,6 +61,7 @@ class Profile(ctypes.Structure):
         ("launches", ctypes.c_int64), ("gemm_calls", ctypes.c_int64 * 3), ("gemm_ms", ctypes.c_double * 3),
         ("gemm_flops", ctypes.c_double * 3), ("slice_ms", ctypes.c_double), ("eig_ms", ctypes.c_double),
         ("step_ms", ctypes.c_double), ("steps", ctypes.c_int64), ("eig_part_ms", ctypes.c_double * 4),
+        ("operand_elems", ctypes.c_double * 3), ("output_elems", ctypes.c_double * 3),
     ]
 
 
@@ -154,9 +156,10 @@ lib = _load()
 
 
 def params(beta, delta, n_max, d_cut, n_steps, h=0.0, h1=0.0, prec=FP64, env_policy=0, m_range=50,
-           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0, side_rtol=0.0, block_sparse=0, q=2):
+           eig_max_sweeps=0, tkind=T_PURE, tie_rtol=0.0, eig_tol=0.0, side_rtol=0.0, block_sparse=0, q=2,
+           eig_mode=0, eig_fp64_iters=0):
     return Params(beta, delta, h, h1, n_max, d_cut, n_steps, prec, env_policy, m_range,
-                  eig_max_sweeps, tkind, tie_rtol, eig_tol, side_rtol, block_sparse, q)
+                  eig_max_sweeps, tkind, tie_rtol, eig_tol, side_rtol, block_sparse, q, eig_mode, eig_fp64_iters)
 
 
 def hotrg_create(workspace_bytes=0, stream=0):

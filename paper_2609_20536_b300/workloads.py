@@ -30,11 +30,14 @@ MEDIUM = Point(1.1, 0.5, 5, 48, 30)           # n_max = 5 (D0 = 11), D_cut = 48,
 
 
 def headline_points(n, seed=SEED, d_cut=64, n_max=4, n_steps=25):
-    """n distinct points, beta ~ U[0.5, 2.0], Delta ~ U[0, 1], at one D_cut."""
+    """n distinct points, beta ~ U[0.5, 2.0], Delta ~ U[0, 1], at one D_cut.
+
+    The pairs are drawn one point at a time, so the first k points are the
+    same for every n >= k (a run of any length starts on the same points).
+    """
     rng = np.random.default_rng(seed)
-    betas = rng.uniform(0.5, 2.0, n)
-    deltas = rng.uniform(0.0, 1.0, n)
-    return [Point(float(b), float(d), n_max, d_cut, n_steps) for b, d in zip(betas, deltas)]
+    bd = rng.uniform((0.5, 0.0), (2.0, 1.0), size=(n, 2))
+    return [Point(float(b), float(d), n_max, d_cut, n_steps) for b, d in bd]
 
 
 def grid_points(nb=64, nd=64, seed=SEED, n_max=4, n_steps=25, dcuts=(24, 32, 48, 64)):

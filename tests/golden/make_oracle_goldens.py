@@ -13,6 +13,9 @@ Cases (one JSON file each, written as soon as the case ends):
   headline0/1    the first two points of the seeded D_cut = 64 workload
                  (beta ~ U[0.5, 2], Delta ~ U[0, 1], seed 20536, drawn one
                  point at a time), n_max = 4, 25 steps
+A case name with the suffix "_strict" reruns that case with the strict widths
+(cut cluster 1e-12, bare eps_2 < eps_1 comparison) and writes
+strict_<case>.json: what the two widths of the reading change.
 
 Dense FP64 on the host: the D_cut = 64 cases hold two D^5 = 1.07e9-element
 intermediates (8.6 GB each) and take about an hour each on eight cores.
@@ -57,7 +60,11 @@ def fnum(x):
 
 
 def run_case(name):
-    beta, delta, n_max, d_cut, n_steps = CASES[name]
+    strict = name.endswith("_strict")
+    base = name[: -len("_strict")] if strict else name
+    beta, delta, n_max, d_cut, n_steps = CASES[base]
+    widths = ({"tie_rtol": OH.STRICT_TIE_RTOL, "side_rtol": OH.STRICT_SIDE_RTOL} if strict
+              else {"tie_rtol": OH.TIE_RTOL, "side_rtol": OH.SIDE_RTOL})
     t_steps = []
     t_last = [time.perf_counter()]
 
@@ -69,14 +76,14 @@ def run_case(name):
               f"strict_same {rec.strict_same} ({t_steps[-1]:.1f} s)", flush=True)
 
     t0 = time.perf_counter()
-    res = OH.run_gxy(beta, delta, n_max, d_cut, n_steps, on_step=on_step)
+    res = OH.run_gxy(beta, delta, n_max, d_cut, n_steps, on_step=on_step, **widths)
     wall = time.perf_counter() - t0
     out = {
-        "case": name,
+        "case": base, "strict": strict,
         "written_by": "tests/golden/make_oracle_goldens.py (FP64 CPU oracle, oracle.hotrg.run_gxy)",
         "passage": "thesis §2.4.1 (Eq. 2.11, 2.12, eps_1/eps_2 rule, Eq. 2.15, 2.16), tensor Eq. 3.4/3.6",
         "beta": beta, "delta": delta, "n_max": n_max, "d_cut": d_cut, "n_steps": n_steps,
-        "tie_rtol": OH.TIE_RTOL, "side_rtol": OH.SIDE_RTOL,
+        "tie_rtol": widths["tie_rtol"], "side_rtol": widths["side_rtol"],
         "strict_tie_rtol": OH.STRICT_TIE_RTOL, "strict_side_rtol": OH.STRICT_SIDE_RTOL,
         "lnz_per_site": res.lnz_per_site, "ln_c0": res.ln_c0, "ln_trace": res.ln_trace,
         "steps": [{"k": k + 1, "Dh": r.Dh, "Dv": r.Dv, "dprime": r.Dp, "ln_c": r.ln_c,
@@ -88,7 +95,7 @@ def run_case(name):
         "wall_s": wall, "step_s": t_steps,
         "host": {"machine": platform.machine(), "cpus": os.cpu_count(), "numpy": np.__version__},
     }
-    path = os.path.join(HERE, f"oracle_{name}.json")
+    path = os.path.join(HERE, f"strict_{base}.json" if strict else f"oracle_{name}.json")
     with open(path + ".tmp", "w") as f:
         json.dump(out, f, indent=1)
     os.replace(path + ".tmp", path)
@@ -97,4 +104,7 @@ def run_case(name):
 
 if __name__ == "__main__":
     for name in sys.argv[1:] or list(CASES):
+        if name.endswith("_strict") and name[: -len("_strict")] not in CASES or (
+                not name.endswith("_strict") and name not in CASES):
+            raise SystemExit(f"unknown case {name}")
         run_case(name)

@@ -79,3 +79,37 @@ def test_autotune_batch_and_tuned_stream_count(H, C):
     single = [C.run([p])[0].lnz_per_site for p in pts]
     got = [r.lnz_per_site for r in C.run_batch(pts, nstreams=0)]  # 0: the tuned count
     assert got == single
+
+
+# A point whose block-sparse products cannot be planned: with n_max = 34 the labels
+# run over [-34, 34] and the first environment's signed label sums span 137 values,
+# more than the planner's 128-slot table, so the device planner records HOTRG_ENOTSUP
+# in that point's status slot (the out-of-table elements are left out of every pass).
+def enotsup_point(H, prec):
+    return H.params(1.0, 0.5, 34, 4, 1, prec=prec, block_sparse=1)
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "SPLIT_BF16"])
+def test_batch_device_failure_fails_that_point_alone(H, C, prec_name):
+    prec = getattr(H, prec_name)
+    good = [H.params(*pt, prec=prec, block_sparse=1) for pt in BATCH[:3]]
+    single = [C.run([p])[0].lnz_per_site for p in good]
+    pts = [good[0], enotsup_point(H, prec), good[1], good[2]]
+    for _ in range(2):  # the second call replays every class from its graph, the failing one too
+        got = H.hotrg_run_batch(C.handle, pts, nstreams=2, check=False)
+        assert got[1].status == H.ENOTSUP
+        assert [got[i].status for i in (0, 2, 3)] == [0, 0, 0]
+        assert [got[i].lnz_per_site for i in (0, 2, 3)] == single
+    # with invalid parameters on the host as well: each failing entry fails alone
+    pts.insert(2, H.params(1.0, 1.5, 2, 12, 4, prec=prec))
+    got = H.hotrg_run_batch(C.handle, pts, nstreams=3, check=False)
+    assert got[1].status == H.ENOTSUP and got[2].status == H.EINVAL
+    assert [got[i].lnz_per_site for i in (0, 3, 4)] == single
+
+
+def test_run_device_failure_does_not_leak_into_the_next_point(H, C):
+    got = H.hotrg_run(C.handle, [enotsup_point(H, H.SPLIT_BF16), H.params(*BATCH[0], prec=H.SPLIT_BF16)],
+                      check=False)
+    assert got[0].status == H.ENOTSUP and got[1].status == 0
+    ref = OH.run_gxy(*BATCH[0]).lnz_per_site
+    assert abs(got[1].lnz_per_site - ref) < 1e-9

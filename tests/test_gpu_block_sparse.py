@@ -12,7 +12,7 @@ import pytest
 from oracle import gxy
 from oracle import hotrg as OH
 
-from parity_points import BATCH, DRIFT_SHAPES, SPLIT_SHAPES
+from parity_points import BATCH, DRIFT_SHAPES, FP64_SHAPES, SPLIT_SHAPES
 
 pytestmark = pytest.mark.gpu
 
@@ -94,10 +94,43 @@ def test_block_sparse_batch_replay_equals_single_runs(H, C):
         assert [r.lnz_per_site for r in got] == single
 
 
-def test_block_sparse_rejects_fp64_form(H, C):
-    with pytest.raises(H.HotrgError) as e:
-        C.run([H.params(1.0, 0.5, 2, 8, 4, prec=H.FP64, block_sparse=1)])
-    assert e.value.status == H.EINVAL
+@pytest.mark.parametrize("beta,delta,nm,dcut,steps", FP64_SHAPES)
+def test_block_sparse_fp64_form_against_oracle(H, C, beta, delta, nm, dcut, steps):
+    # the FP64 form per charge block (the block-sparse remark of §2.3.1 with FP64 FMA):
+    # the FP64 parity bar of the dense FP64 form, per step and for ln Z / N
+    ref = OH.run_gxy(beta, delta, nm, dcut, steps)
+    bs = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.FP64, block_sparse=1)])[0]
+    dense = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.FP64)])[0]
+    assert bs.status == 0
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-10, bs.lnz_per_site - ref.lnz_per_site
+    assert abs(bs.lnz_per_site - dense.lnz_per_site) <= 1e-12
+    for k, rs in enumerate(ref.steps):
+        g = bs.step[k]
+        assert g.dprime == rs.Dp
+        assert abs(g.ln_c - rs.ln_c) <= 1e-11 * max(1.0, abs(rs.ln_c)), (k, g.ln_c, rs.ln_c)
+        assert abs(g.eps_left - rs.eps_left) <= 1e-13 + 1e-8 * abs(rs.eps_left)
+
+
+def test_block_sparse_fp64_form_z2_and_ising(H, C):
+    ref = OH.run_gxy(1.1, 0.4, 3, 16, 14, h1=0.03)
+    bs = C.run([H.params(1.1, 0.4, 3, 16, 14, h1=0.03, prec=H.FP64, block_sparse=1)])[0]
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-10
+    ref = OH.hotrg_run(gxy.ising_tensor(0.6), gxy.ising_charges(), 30, 16, "z2")
+    bs = C.run([H.params(0.6, 0.0, 0, 16, 30, tkind=H.T_ISING, prec=H.FP64, block_sparse=1)])[0]
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= 1e-10
+
+
+def test_block_sparse_fp64_form_counts_block_flops(H, C):
+    p = H.params(1.0, 0.5, 2, 16, 12, prec=H.FP64, block_sparse=1)
+    H.hotrg_profile_enable(C.handle, True)
+    C.run([p])
+    bs = H.hotrg_profile_read(C.handle)
+    H.hotrg_profile_enable(C.handle, True)
+    C.run([H.params(1.0, 0.5, 2, 16, 12, prec=H.SPLIT_BF16, block_sparse=1)])
+    split = H.hotrg_profile_read(C.handle)
+    H.hotrg_profile_enable(C.handle, False)
+    # the same planner: the same algorithmic block flops in both forms
+    assert bs.gemm_flops[1] == split.gemm_flops[1] and bs.gemm_flops[0] == split.gemm_flops[0]
 
 
 def test_block_sparse_profile_counts_block_flops(H, C):
