@@ -94,8 +94,10 @@ typedef struct {
                             the rounding of the eigenvalue sums */
     int32_t block_sparse; /* 1: the environments (A, B, E) and the coarse contraction (s1, s2, s3)
                              run per charge block (the U(1) or Z2 structure of the block-sparse remark
-                             of §2.3.1), in every precision form (HOTRG_FP64: FP64 FMA per block);
-                             pure runs only: with an impurity tensor or h != 0 it has no effect.  The
+                             of §2.3.1), in every precision form (HOTRG_FP64: FP64 FMA per block).
+                             It has no effect with h != 0 (no conserved label), nor on impurity runs
+                             except the cos(2 theta) impurity (Eq. 3.21) at h = 0, h1 != 0, which keeps
+                             the pure tensor's charge parity and so runs in the Z2 block form.  The
                              result equals the dense form's up to the rounding of the form (the FP64
                              form sums each block's products in the same K order as the dense one, but
                              over the block's elements only).  The planner's value table follows each
@@ -113,7 +115,7 @@ typedef struct {
                             (the FP64 form uses this path for U(1) labels and Jacobi on every block for
                             Z2 or no symmetry).  1: FP64 Jacobi on every block (all eigenpairs). */
     int32_t eig_fp64_iters; /* FP64 subspace iterations after the first Rayleigh-Ritz step: 0 = the
-                               form's default (3 for HOTRG_FP64, none for the split forms), 1..8 that
+                               form's default (6 for HOTRG_FP64, none for the split forms), 1..8 that
                                many, -1 none */
 } hotrg_params;
 
@@ -237,6 +239,27 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
  * seconds (may be NULL, max_streams entries) the timed runs.  Synchronous. */
 hotrg_status hotrg_autotune_batch(hotrg_ctx* ctx, const hotrg_params* sample, int32_t npoints,
                                   int32_t max_streams, int32_t* best, double* seconds);
+
+/* Tile shape of the split forms' block-sparse tensor-core products (no
+ * counterpart in the thesis): every output tile has 128 rows and
+ * env_tile_n (environment products) or coarse_tile_n (s1, s2, s3) columns,
+ * 128 or 64.  The 64-column tile wastes less of a thin charge block's padding
+ * and keeps two TMEM accumulator sets, so the next tile's products run while
+ * the previous tile is written out; the 128-column tile issues half as many
+ * B loads per row of A.  The results of the two shapes agree to the split
+ * form's rounding.  The FP64 form always uses 128 x 128 tiles.  Default:
+ * 128 and 128.  Errors: HOTRG_EINVAL for other widths. */
+hotrg_status hotrg_set_tiles(hotrg_ctx* ctx, int32_t env_tile_n, int32_t coarse_tile_n);
+
+/* Autotuner of the tile shapes: runs the sample points (host array, pure
+ * tensors) through hotrg_run_batch with nstreams worker streams (0: the
+ * tuned count) for each of the four (env, coarse) width pairs in the order
+ * (128,128), (128,64), (64,128), (64,64) -- each once untimed (graphs of
+ * the new shapes) and once timed on the host clock -- and keeps the fastest
+ * pair in the context.  env_tile_n, coarse_tile_n (may be NULL) receive it,
+ * seconds (may be NULL, 4 entries) the timed runs.  Synchronous. */
+hotrg_status hotrg_autotune_tiles(hotrg_ctx* ctx, const hotrg_params* sample, int32_t npoints, int32_t nstreams,
+                                  int32_t* env_tile_n, int32_t* coarse_tile_n, double* seconds);
 
 /* Observables of npoints points (§3.4): ln Z/N and f at zero field;
  * C_V = beta^2 [l(beta+hb) - 2 l(beta) + l(beta-hb)] / hb^2 (Eq. 3.17);

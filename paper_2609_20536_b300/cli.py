@@ -6,6 +6,7 @@
   python -m paper_2609_20536_b300.cli surrogate [--nb 12 --nd 8 --d-cut 12 --steps 16]
   python -m paper_2609_20536_b300.cli phase --delta 0.32 [--t-lo 0.5 --t-hi 1.2 --n-t 36 --hbar 0.005,0.01,0.02,0.04]
   python -m paper_2609_20536_b300.cli peaks
+  python -m paper_2609_20536_b300.cli sweep --delta 0.3 [--b-lo 0.8 --b-hi 1.6 --b-step 0.01 --n-max 6 --d-cut 96 --steps 30]
 
 `run` prints ln Z/N and the per-step scalars of one point; `grid` times a
 sample of the 64 x 64 (beta, Delta) grid with D_cut drawn from {24, 32, 48,
@@ -14,7 +15,10 @@ observables, trains the MLP ensemble, audits it against HOTRG on random
 points and refines near the C_V / chi maxima; `phase` scans one Delta in
 temperature and prints the C_V peaks, the chi peak at each central field and
 the zero-field T_c of the fit T_p = a + b hbar^c (a row of Table 3.1 at this
-bond dimension); `peaks` measures cuBLAS's dense GEMM rates (torch.matmul)
+bond dimension); `sweep` runs a beta sweep at one Delta with C_V by FP64
+central differences of ln Z/N and the impurity observables m, chi (cos theta,
+h != 0: no conserved label) and m1, chi1 (cos 2 theta, h1 != 0: Z2 blocks),
+each family at its own D_cut; `peaks` measures cuBLAS's dense GEMM rates (torch.matmul)
 in FP64, FP32, TF32 and BF16, the denominators of the FP64-form rooflines;
 `contract` times one C = A B^T of the given
 shape through the contraction engine (random FP64 operands generated on the
@@ -78,8 +82,14 @@ def main(argv=None):
                         "report |d lnZ/N| against it")
     g.add_argument("--out", default="", help="write every point's (beta, Delta, D_cut, lnZ/N, status) as JSON here")
     sg = sub.add_parser("surrogate")
-    sg.add_argument("--nb", type=int, default=12, help="training grid: nb betas in [0.6, 1.6]")
-    sg.add_argument("--nd", type=int, default=8, help="training grid: nd Deltas in [0.1, 0.9]")
+    sg.add_argument("--nb", type=int, default=12, help="training grid: nb betas in [b-lo, b-hi]")
+    sg.add_argument("--nd", type=int, default=8, help="training grid: nd Deltas in [d-lo, d-hi]")
+    sg.add_argument("--b-lo", type=float, default=0.6)
+    sg.add_argument("--b-hi", type=float, default=1.6)
+    sg.add_argument("--d-lo", type=float, default=0.1)
+    sg.add_argument("--d-hi", type=float, default=0.9)
+    sg.add_argument("--per-peak", type=int, default=4, help="refinement points per C_V or chi window and Delta")
+    sg.add_argument("--out", default="", help="write the training, audit and refinement tables as JSON here")
     sg.add_argument("--n-max", type=int, default=2)
     sg.add_argument("--d-cut", type=int, default=12)
     sg.add_argument("--steps", type=int, default=16)
@@ -102,6 +112,23 @@ def main(argv=None):
     ph.add_argument("--nstreams", type=int, default=0)
     ph.add_argument("--chi-prominence", type=float, default=0.0, help="least prominence of a chi peak")
     ph.add_argument("--cv-prominence", type=float, default=0.0, help="least prominence of a listed C_V peak")
+    sw = sub.add_parser("sweep")
+    sw.add_argument("--delta", type=float, default=0.3)
+    sw.add_argument("--b-lo", type=float, default=0.8)
+    sw.add_argument("--b-hi", type=float, default=1.6)
+    sw.add_argument("--b-step", type=float, default=0.01)
+    sw.add_argument("--n-max", type=int, default=6)
+    sw.add_argument("--d-cut", type=int, default=96, help="D_cut of the pure runs (ln Z/N, f, C_V)")
+    sw.add_argument("--m-d-cut", type=int, default=0, help="D_cut of the cos theta runs (m, chi); 0: skip them")
+    sw.add_argument("--m1-d-cut", type=int, default=0, help="D_cut of the cos 2 theta runs (m1, chi1); 0: skip")
+    sw.add_argument("--steps", type=int, default=30)
+    sw.add_argument("--hb", type=float, default=1e-3)
+    sw.add_argument("--hbar", type=float, default=0.01)
+    sw.add_argument("--dh", type=float, default=1e-3)
+    sw.add_argument("--prec", default="split", choices=["split", "fast", "fp64"])
+    sw.add_argument("--nstreams", type=int, default=1,
+                    help="worker streams (each holds a full workspace: keep 1 at D_cut = 96)")
+    sw.add_argument("--out", default="")
     pk = sub.add_parser("peaks")
     pk.add_argument("--repeat", type=int, default=5)
     c = sub.add_parser("contract")
@@ -220,35 +247,100 @@ def main(argv=None):
         def mk(b, d):
             return H.params(b, d, a.n_max, a.d_cut, a.steps, prec=prec, block_sparse=1)
 
-        betas, deltas = np.linspace(0.6, 1.6, a.nb), np.linspace(0.1, 0.9, a.nd)
+        betas, deltas = np.linspace(a.b_lo, a.b_hi, a.nb), np.linspace(a.d_lo, a.d_hi, a.nd)
         X = np.array([[b, d] for d in deltas for b in betas])
         t0 = time.perf_counter()
         obs = ctx.observables_batch([mk(b, d) for b, d in X], nstreams=0)
         out["train_points"], out["train_observables_s"] = len(X), time.perf_counter() - t0
+        out["hotrg_points_per_s"] = len(X) / out["train_observables_s"]
         Y = np.array([[o.f, o.cv, o.chi, o.chi1] for o in obs])
         sur = H.Surrogate(ensemble=4, seed=20536)
         t0 = time.perf_counter()
         out["final_loss"] = sur.fit(X, Y, epochs=a.epochs, batch=64, lr=2e-3)
         out["fit_s"] = time.perf_counter() - t0
         rng = np.random.default_rng(7)
-        Xa = np.column_stack([rng.uniform(0.6, 1.6, a.audit), rng.uniform(0.1, 0.9, a.audit)])
-        t0 = time.perf_counter()
+        Xa = np.column_stack([rng.uniform(a.b_lo, a.b_hi, a.audit), rng.uniform(a.d_lo, a.d_hi, a.audit)])
         pred, sd = sur.predict(Xa)
-        out["predictions_per_s"] = len(Xa) / (time.perf_counter() - t0)
+        Xt = np.column_stack([rng.uniform(a.b_lo, a.b_hi, 65536), rng.uniform(a.d_lo, a.d_hi, 65536)])
+        sur.predict(Xt[:1024])
+        t0 = time.perf_counter()
+        sur.predict(Xt)
+        out["predictions_per_s"] = len(Xt) / (time.perf_counter() - t0)
         ref = ctx.observables_batch([mk(b, d) for b, d in Xa], nstreams=0)
         R = np.array([[o.f, o.cv, o.chi, o.chi1] for o in ref])
         err = np.abs(pred - R) / np.array(sur.scaling.y_std[:])
         out["audit_std_err_max"] = err.max(0).tolist()
         out["audit_std_err_rms"] = np.sqrt((err ** 2).mean(0)).tolist()
         out["audit_spread_median"] = float(np.median(sd.max(1)))
-        Xr, pk = sur.peaks(deltas, 0.6, 1.6, 201, 4, 0.05)
+        Xr, pk = sur.peaks(deltas, a.b_lo, a.b_hi, 401, a.per_peak, 0.05)
         t0 = time.perf_counter()
-        _, _, solved = sur.refine(ctx, mk(1.0, 0.5), Xr, threshold=a.threshold, nstreams=0)
+        yr, sdr, solved = sur.refine(ctx, mk(1.0, 0.5), Xr, threshold=a.threshold, nstreams=0)
         out["refine_points"], out["refine_resolved"] = len(Xr), int(solved.sum())
         out["refine_s"] = time.perf_counter() - t0
+        # the surrogate's own answer on the refinement points, judged by HOTRG where HOTRG re-solved
+        ys, _ = sur.predict(Xr)
+        if solved.any():
+            errs = np.abs(ys[solved] - yr[solved]) / np.array(sur.scaling.y_std[:])
+            out["refine_resolved_std_err_rms"] = np.sqrt((errs ** 2).mean(0)).tolist()
+        out["refine_kept_surrogate"] = int((~solved).sum())
+        if (~solved).any():
+            out["refine_kept_spread_max"] = float(sdr[~solved].max())
         out["peak_beta_cv_chi"] = pk.tolist()
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump({"X": X.tolist(), "Y": Y.tolist(), "Xa": Xa.tolist(), "Ya": R.tolist(), "pred_a": pred.tolist(),
+                           "Xr": Xr.tolist(), "yr": yr.tolist(), "solved": solved.tolist()}, f)
         sur.close()
         print(json.dumps(out))
+    elif a.cmd == "sweep":
+        import numpy as np
+        nb = int(round((a.b_hi - a.b_lo) / a.b_step)) + 1
+        betas = [a.b_lo + i * a.b_step for i in range(nb)]
+
+        def runs(plist, imp):
+            t0 = time.perf_counter()
+            if a.nstreams > 1:
+                r = H.hotrg_run_batch(ctx.handle, plist, imp_kind=imp, nstreams=a.nstreams, check=False)
+            else:
+                r = H.hotrg_run(ctx.handle, plist, imp_kind=imp, check=False)
+            return r, time.perf_counter() - t0
+
+        def mk(b, dc, h=0.0, h1=0.0):
+            return H.params(b, a.delta, a.n_max, dc, a.steps, h=h, h1=h1, prec=prec, block_sparse=1)
+
+        out = {"delta": a.delta, "n_max": a.n_max, "steps": a.steps, "prec": a.prec, "hb": a.hb, "hbar": a.hbar,
+               "dh": a.dh, "beta": betas, "d_cut": a.d_cut}
+        pure, t = runs([mk(b + o, a.d_cut) for b in betas for o in (-a.hb, 0.0, a.hb)], H.T_PURE)
+        lz = np.array([r.lnz_per_site for r in pure]).reshape(nb, 3)
+        out["pure_runs"], out["pure_s"] = 3 * nb, t
+        out["status_pure"] = sorted(set(r.status for r in pure))
+        out["lnz"] = lz[:, 1].tolist()
+        out["f"] = (-lz[:, 1] / np.array(betas)).tolist()
+        out["cv"] = (np.array(betas) ** 2 * (lz[:, 2] - 2 * lz[:, 1] + lz[:, 0]) / a.hb ** 2).tolist()
+        for name, dc, kind in (("m", a.m_d_cut, H.T_IMP_M), ("m1", a.m1_d_cut, H.T_IMP_M1)):
+            if dc <= 0:
+                continue
+            fld = (lambda v: {"h": v}) if name == "m" else (lambda v: {"h1": v})
+            rr, t = runs([mk(b, dc, **fld(a.hbar + o)) for b in betas for o in (-a.dh, 0.0, a.dh)], kind)
+            m = np.array([r.imp_ratio for r in rr]).reshape(nb, 3)
+            out[name] = m[:, 1].tolist()
+            out["chi" if name == "m" else "chi1"] = ((m[:, 2] - m[:, 0]) / (2 * a.dh)).tolist()
+            out[name + "_d_cut"], out[name + "_runs"], out[name + "_s"] = dc, 3 * nb, t
+            out["status_" + name] = sorted(set(r.status for r in rr))
+        cvp, _ = H.hotrg_find_peaks(np.array(betas), np.array(out["cv"]), 0.0, 4)
+        out["cv_peaks_beta"] = [x for x, _, _ in cvp]
+        # C_V < 0 cannot be physical: the kept set changed between beta - hb and beta + hb (a kink of
+        # the truncated ln Z); such samples, and peaks next to them, are truncation artefacts
+        cv = np.array(out["cv"])
+        out["cv_negative_beta"] = [b for b, v in zip(betas, cv) if v < 0]
+        for key in ("chi", "chi1"):
+            if key in out:
+                pk_, _ = H.hotrg_find_peaks(np.array(betas), np.array(out[key]), 0.0, 4)
+                out[key + "_peaks_beta"] = [x for x, _, _ in pk_]
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(out, f)
+        print(json.dumps({k: v for k, v in out.items() if not isinstance(v, list) or len(v) < 8}))
     elif a.cmd == "phase":
         import numpy as np
         temps = np.linspace(a.t_lo, a.t_hi, a.n_t)

@@ -192,8 +192,17 @@ static hotrg_status check_params(hotrg_ctx* ctx, const hotrg_params* p) {
 
 static int d0_of(const hotrg_params* p) { return p->tkind == HOTRG_T_ISING ? 2 : 2 * p->n_max + 1; }
 
+// Whether an impurity run can take the block-sparse path: the impurity tensor must obey the
+// pure tensor's symmetry.  With h = 0 and h1 != 0 (Z2: charge parity) the cos(2 theta)
+// impurity of Eq. 3.21 changes the charge by an even amount, so it keeps the parity rule; the
+// cos(theta) impurity (odd) and every impurity at h = h1 = 0 (U(1): charge changed by 1 or 2)
+// do not.
+static bool imp_blocks_ok(const hotrg_params* p, int imp_kind) {
+    return p->tkind != HOTRG_T_ISING && imp_kind == HOTRG_T_IMP_M1 && sym_of(p) == SYM_Z2;
+}
+
 // Workspace bytes of one step with the given sizes (everything except T in/out).
-static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
+static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp, bool imp_blocks) {
     const size_t n = (size_t)Dh * Dh;
     const size_t Dp = std::min<size_t>(p->d_cut, n);
     const size_t d4 = (size_t)Dh * Dh * Dv * Dv;
@@ -215,7 +224,7 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp) {
     size_t g = 0;
     // the dense engine is needed unless every product of the step runs per block (the same
     // condition as do_step's)
-    const bool blocks = p->block_sparse && !imp && sym_of(p) != SYM_NONE;
+    const bool blocks = p->block_sparse && (!imp || imp_blocks) && sym_of(p) != SYM_NONE;
     if (!blocks)
         for (auto& sh : shapes) g = std::max(g, gemm_engine_workspace(p->prec, sh[0], sh[1], sh[2]));
     if (blocks) {
@@ -311,7 +320,8 @@ static hotrg_status environment_blocks(hotrg_ctx* ctx, int prec, int sym, const 
     auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const double* X, const double* Y, double* C) {
         const size_t mark = ctx->ws.used;
         BsPlan pl;
-        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_ENV, pl, prec == HOTRG_FP64 ? INT32_MAX : 0);
+        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_ENV, pl, prec == HOTRG_FP64 ? INT32_MAX : 0,
+                                  prec == HOTRG_FP64 ? 128 : ctx->tile_n[0]);
         if (st == HOTRG_OK) st = grouped_engine(ctx, prec, pl, X, 0, Y, 0, C, 0, PROF_GEMM_ENV);
         ctx->ws.used = mark;
         return st;
@@ -434,7 +444,8 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
                    void* C, int cf) {
         const size_t mark = ctx->ws.used;
         BsPlan pl;
-        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl, prec == HOTRG_FP64 ? INT32_MAX : 0);
+        hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl, prec == HOTRG_FP64 ? INT32_MAX : 0,
+                                  prec == HOTRG_FP64 ? 128 : ctx->tile_n[1]);
         if (st == HOTRG_OK) st = grouped_engine(ctx, prec, pl, A, af, B, 0, C, cf, PROF_GEMM_COARSE);
         ctx->ws.used = mark;
         return st;
@@ -471,10 +482,12 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
     return HOTRG_OK;
 }
 
+// imp_blocks: the impurity tensor keeps the pure tensor's block rule (imp_blocks_ok), so its
+// co-update may run per charge block too.
 static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double* T_in, const int32_t* q_h,
                             const int32_t* q_v, int Dh, int Dv, double* T_out, int32_t* q_out, int* dprime,
                             hotrg_step_info* info, const double* Ti_in, double* Ti_out, double* lnz_acc,
-                            double weight) {
+                            double weight, bool imp_blocks) {
     (void)q_v;
     const int prec = p->prec;
     const int64_t n = (int64_t)Dh * Dh;
@@ -511,7 +524,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     hotrg_status s;
     const int h_step = prof_begin(ctx);
     const int sym = sym_of(p);
-    const bool blocks = p->block_sparse && !Ti_in && sym != SYM_NONE;
+    const bool blocks = p->block_sparse && (!Ti_in || imp_blocks) && sym != SYM_NONE;
     if (blocks) {
         if ((s = environment_blocks(ctx, prec, sym, T_in, q_h, q_v, Dh, Dv, false, A2, B2, EL)) != HOTRG_OK)
             return s;
@@ -539,7 +552,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     // list at least twice the states they keep, so the iteration converges fast); with Z2 or no
     // symmetry it solves every block by Jacobi; eig_mode = 1 asks for Jacobi everywhere
     plan.exact = p->eig_mode == 1 || (prec == HOTRG_FP64 && plan.sym != SYM_U1);
-    plan.fp64_iters = p->eig_fp64_iters > 0 ? p->eig_fp64_iters : (p->eig_fp64_iters < 0 ? 0 : (prec == HOTRG_FP64 ? 3 : 0));
+    plan.fp64_iters = p->eig_fp64_iters > 0 ? p->eig_fp64_iters : (p->eig_fp64_iters < 0 ? 0 : (prec == HOTRG_FP64 ? 6 : 0));
     const int h_eig = prof_begin(ctx);
     if ((s = eig_truncate(ctx, plan, EL, p->env_policy == 0 ? ER : nullptr, q_h, P, q_out, info, eigws)) !=
         HOTRG_OK)
@@ -555,10 +568,19 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     launch_norm(T_out, tn, partial, norm, ctx->stream);
     if (Ti_in) {
         // T_imp' = [P^T (T_imp above T) P + P^T (T above T_imp) P] / (2 c_k)
-        if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, Ti_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, Ti_out)) != HOTRG_OK)
-            return s;
-        if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, Ti_in, Pt, Pt2, Tt, Tb, W, W2, Tc, Ti2)) != HOTRG_OK)
-            return s;
+        if (blocks) {
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Tc, Ti_out)) !=
+                HOTRG_OK)
+                return s;
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Tc, Ti2)) !=
+                HOTRG_OK)
+                return s;
+        } else {
+            if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, Ti_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, Ti_out)) != HOTRG_OK)
+                return s;
+            if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, Ti_in, Pt, Pt2, Tt, Tb, W, W2, Tc, Ti2)) != HOTRG_OK)
+                return s;
+        }
         launch_axpby(Ti_out, Ti2, 0.5, 0.5, tn, ctx->stream);
         launch_scale_inv(Ti_out, tn, norm, ctx->stream);
     }
@@ -633,7 +655,7 @@ static size_t point_bytes(const hotrg_params* p, int imp_kind, PointPlan& pl) {
     for (size_t k = 0; k < pl.dh.size(); ++k) {
         const size_t Dp = std::min<size_t>(p->d_cut, (size_t)pl.dh[k] * pl.dh[k]);
         tmax = std::max(tmax, Dp * Dp * pl.dv[k] * pl.dv[k]);
-        smax = std::max(smax, step_bytes(p, pl.dh[k], pl.dv[k], pl.imp));
+        smax = std::max(smax, step_bytes(p, pl.dh[k], pl.dv[k], pl.imp, imp_blocks_ok(p, imp_kind)));
     }
     pl.qmax = std::max(pl.D0, p->d_cut) + 1;
     const size_t fixed = a256(tmax * 8) * (pl.imp ? 4 : 2) + a256(pl.qmax * 4) * 3 + a256(16384) +
@@ -678,6 +700,7 @@ static hotrg_status enqueue_point(hotrg_ctx* ctx, const hotrg_params* p, int imp
     StatusSlot slot(ctx, &pl.rd->status);
     const int D0 = pl.D0;
     const bool imp = pl.imp;
+    const bool imp_blocks = imp && imp_blocks_ok(p, imp_kind);
     hotrg_status s;
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(pl.rd, 0, sizeof(RunDev), st));
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(pl.infos, 0, sizeof(hotrg_step_info) * HOTRG_MAX_STEPS, st));
@@ -705,7 +728,7 @@ static hotrg_status enqueue_point(hotrg_ctx* ctx, const hotrg_params* p, int imp
         ctx->ws.used = pl.step_base;
         int dp = 0;
         s = do_step(ctx, p, Tcur, qh, qv, pl.dh[k], pl.dv[k], Tnext, qspare, &dp, &pl.infos[k], Icur, Inext,
-                    &pl.rd->lnz, ldexp(1.0, -(k + 1)));
+                    &pl.rd->lnz, ldexp(1.0, -(k + 1)), imp_blocks);
         if (s != HOTRG_OK) return s;
         // new horizontal labels = old vertical labels; new vertical = q_out
         int32_t* old_h = qh;
@@ -1005,9 +1028,9 @@ hotrg_status hotrg_step(hotrg_ctx* ctx, const hotrg_params* p, const double* T_i
     if (Dh < 1 || Dv < 1 || Dh > 128 || Dv > 128) return set_err(ctx, HOTRG_EINVAL, "Dh, Dv must lie in [1, 128]");
     if (T_out == T_in) return set_err(ctx, HOTRG_EINVAL, "T_out aliases T_in");
     const bool imp = T_imp_in != nullptr;
-    if ((s = ws_reserve(ctx, step_bytes(p, Dh, Dv, imp) + 4096)) != HOTRG_OK) return s;
+    if ((s = ws_reserve(ctx, step_bytes(p, Dh, Dv, imp, false) + 4096)) != HOTRG_OK) return s;
     int dp = 0;
-    s = do_step(ctx, p, T_in, q_h, q_v, Dh, Dv, T_out, q_out, &dp, info_dev, T_imp_in, T_imp_out, nullptr, 0.0);
+    s = do_step(ctx, p, T_in, q_h, q_v, Dh, Dv, T_out, q_out, &dp, info_dev, T_imp_in, T_imp_out, nullptr, 0.0, false);
     *dprime = dp;
     if (s == HOTRG_OK) {
         fold_status_kernel<<<1, 32, 0, ctx->stream>>>(info_dev, ctx->status_dev);
@@ -1114,6 +1137,14 @@ hotrg_status hotrg_run_batch(hotrg_ctx* ctx, const hotrg_params* params, int32_t
         }
         HOTRG_CUDA_TRY(ctx, cudaStreamWaitEvent(w.stream, B->fork, 0));
     }
+    for (Worker& w : B->workers)
+        if (w.ctx->tile_n[0] != ctx->tile_n[0] || w.ctx->tile_n[1] != ctx->tile_n[1]) {
+            // the captured graphs hold the previous tile shapes' kernels
+            for (auto& g : w.graphs) cudaGraphExecDestroy(g.exec);
+            w.graphs.clear();
+            w.ctx->tile_n[0] = ctx->tile_n[0];
+            w.ctx->tile_n[1] = ctx->tile_n[1];
+        }
     for (Worker& w : B->workers)
         if (w.ctx->ws.cap < need) {
             for (auto& g : w.graphs) cudaGraphExecDestroy(g.exec);  // their buffers move
@@ -1405,6 +1436,52 @@ hotrg_status hotrg_autotune_batch(hotrg_ctx* ctx, const hotrg_params* sample, in
     }
     ctx->tuned_streams = kbest;
     if (best) *best = kbest;
+    return HOTRG_OK;
+}
+
+hotrg_status hotrg_set_tiles(hotrg_ctx* ctx, int32_t env_tile_n, int32_t coarse_tile_n) {
+    if (!ctx) return HOTRG_EINVAL;
+    ctx->last_error.clear();
+    if ((env_tile_n != 64 && env_tile_n != 128) || (coarse_tile_n != 64 && coarse_tile_n != 128))
+        return set_err(ctx, HOTRG_EINVAL, "tile widths must be 64 or 128");
+    ctx->tile_n[0] = env_tile_n;
+    ctx->tile_n[1] = coarse_tile_n;
+    return HOTRG_OK;
+}
+
+hotrg_status hotrg_autotune_tiles(hotrg_ctx* ctx, const hotrg_params* sample, int32_t npoints, int32_t nstreams,
+                                  int32_t* env_tile_n, int32_t* coarse_tile_n, double* seconds) {
+    if (!ctx) return HOTRG_EINVAL;
+    ctx->last_error.clear();
+    if (!sample || npoints < 1 || nstreams < 0 || nstreams > 16)
+        return set_err(ctx, HOTRG_EINVAL, "need npoints >= 1 and nstreams in [0, 16]");
+    const int widths[2] = {128, 64};
+    std::vector<hotrg_result> res((size_t)npoints);
+    double tbest = 0.0;
+    int ebest = 128, cbest = 128, k = 0;
+    for (int e : widths)
+        for (int c : widths) {
+            ctx->tile_n[0] = e;
+            ctx->tile_n[1] = c;
+            // untimed: the workers rebuild their graphs for the new shapes; then timed
+            hotrg_status s = hotrg_run_batch(ctx, sample, npoints, HOTRG_T_PURE, nstreams, res.data());
+            if (s != HOTRG_OK) return s;
+            const auto t0 = std::chrono::steady_clock::now();
+            s = hotrg_run_batch(ctx, sample, npoints, HOTRG_T_PURE, nstreams, res.data());
+            if (s != HOTRG_OK) return s;
+            const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (seconds) seconds[k] = t;
+            ++k;
+            if (k == 1 || t < tbest) {
+                tbest = t;
+                ebest = e;
+                cbest = c;
+            }
+        }
+    ctx->tile_n[0] = ebest;
+    ctx->tile_n[1] = cbest;
+    if (env_tile_n) *env_tile_n = ebest;
+    if (coarse_tile_n) *coarse_tile_n = cbest;
     return HOTRG_OK;
 }
 

@@ -12,7 +12,7 @@
 // order), and lays out one group per value present in both M and N:
 //   rows of the group  -> positions mbase .. mbase + M_g - 1 of the sorted M list
 //   padded slice rows  -> mpad .. mpad + round_up(M_g, 128) - 1
-//   tiles              -> tile_base .. + ceil(M_g/128) ceil(N_g/128) - 1.
+//   tiles              -> tile_base .. + ceil(M_g/128) ceil(N_g/tile_n) - 1 (tile_n = 128 or 64).
 // For every position it stores the two element offsets the engine needs
 // (operand and output for M and N, A and B for K).  Groups whose value has
 // no element of K still get tiles: their block of C is zero and is written.
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
                                                        int32_t* __restrict__ sM, int32_t* __restrict__ sK,
                                                        int32_t* __restrict__ sN, BsGroup* __restrict__ groups,
                                                        BsHeader* __restrict__ hdr, double* prof_acc, int prof_class,
-                                                       int kp_cap, int32_t* status) {
+                                                       int kp_cap, int tile_n, int32_t* status) {
     __shared__ int64_t tot[3][BS_V], base[3][BS_V];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int v = threadIdx.x;  // thread 0 below builds the group table
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
             }
             g.mpad = mpad;
             g.npad = npad;
-            g.tiles_n = (g.N + 127) / 128;
+            g.tiles_n = (g.N + tile_n - 1) / tile_n;
             g.tile_base = (int32_t)tiles;
             mpad += (g.M + 127) / 128 * 128;
             npad += (g.N + 127) / 128 * 128;
@@ -273,7 +273,8 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN) {
 }
 
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
-                     BsPlan& out, int32_t kp_cap_override) {
+                     BsPlan& out, int32_t kp_cap_override, int tile_n) {
+    if (tile_n != 64 && tile_n != 128) return set_err(ctx, HOTRG_EINVAL, "tile width must be 64 or 128");
     const BsSet* sets[3] = {&M, &K, &N};
     int32_t* counts[3];
     int32_t* starts[3];
@@ -305,7 +306,7 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
     // sets, whose blocks hold a small fraction of K (the device checks every block against it)
     out.kp_cap = kp_cap_override > 0 ? kp_cap_override : bs_pitch(K.size, sym);
     bs_scan_kernel<<<1, BS_SCAN_THREADS, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
-                                      starts[2], out.groups, out.hdr, facc, prof_class, out.kp_cap, st);
+                                      starts[2], out.groups, out.hdr, facc, prof_class, out.kp_cap, tile_n, st);
     for (int i = 0; i < 3; ++i) {
         const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
         bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], centre, offs[i][0],
@@ -319,6 +320,7 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
     out.offK1 = offs[1][1];
     out.offN0 = offs[2][0];
     out.offN1 = offs[2][1];
+    out.tile_n = tile_n;
     out.nM = M.size;
     out.nK = K.size;
     out.nN = N.size;

@@ -508,12 +508,13 @@ __device__ __forceinline__ float block_sum_f32(float v, float* red) {
 // spread over the warps, the update and the norms over all threads.  Same
 // algorithm (two classical Gram-Schmidt passes, dependent columns replaced by
 // hashed random columns, at most four attempts), fixed reduction order.
-__device__ void cgs2_block_t(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* rbuf, float* red) {
+__device__ void cgs2_block_t(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* rbuf, float* red,
+                             int attempts) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < b; ++j) {
         float* yj = Yt + (int64_t)j * m;
         bool done = false;
-        for (int attempt = 0; attempt < 4 && !done; ++attempt) {
+        for (int attempt = 0; attempt < attempts && !done; ++attempt) {
             if (attempt > 0) {
                 for (int t = tid; t < m; t += blockDim.x)
                     yj[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)j);
@@ -558,7 +559,7 @@ __device__ void cgs2_block_t(float* Yt, int m, int b, uint32_t salt, float dep_t
 // FP32 block subspace iteration on one block: Qt, Yt are b x m (transposed);
 // the product Yt = (E_q Q)^T and the orthonormalisation run on all warps.
 __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double* EL, const double* ER, int n,
-                                                                    int iters, EigWs w) {
+                                                                    int iters, int dep_attempts, EigWs w) {
     __shared__ float Es[32][65];
     __shared__ float Qs[BCAP_MAX][65];
     __shared__ float rbuf[BCAP_MAX];
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
         for (int64_t idx = threadIdx.x; idx < (int64_t)b * m; idx += blockDim.x)
             Q[idx] = hash_unit((uint32_t)(idx % m), (uint32_t)(idx / m));
         __syncthreads();
-        cgs2_block_t(Q, m, b, 1u, 1e-3f, rbuf, red);
+        cgs2_block_t(Q, m, b, 1u, 1e-3f, rbuf, red, 4);
         for (int it = 0; it < iters; ++it) {
             // Yt[j][i] = sum_k Ef[i][k] Qt[j][k], tiles of 32 rows x 64 k
             for (int r0 = 0; r0 < m; r0 += 32) {
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
                 }
             }
             __syncthreads();
-            cgs2_block_t(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, rbuf, red);
+            cgs2_block_t(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, rbuf, red, dep_attempts);
             float* t = Q;  // the orthonormal Y becomes the next Q
             Q = Y;
             Y = t;
@@ -677,7 +678,8 @@ __device__ void proj_warp(float* Yt, int m, int c, int lo, int hi) {
     }
 }
 
-__device__ void bcgs2_block(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* R, float* n0) {
+__device__ void bcgs2_block(float* Yt, int m, int b, uint32_t salt, float dep_tol, float* R, float* n0,
+                            int attempts) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     for (int p0 = 0; p0 < b; p0 += BCGS_PW) {
         const int pw = min(BCGS_PW, b - p0);
@@ -714,7 +716,7 @@ __device__ void bcgs2_block(float* Yt, int m, int b, uint32_t salt, float dep_to
                 float* yc = Yt + c * m;
                 float ref = n0[c - p0];
                 bool done = false;
-                for (int attempt = 0; attempt < 4 && !done; ++attempt) {
+                for (int attempt = 0; attempt < attempts && !done; ++attempt) {
                     if (attempt > 0) {
                         for (int t = lane; t < m; t += 32)
                             yc[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)c);
@@ -746,7 +748,7 @@ __device__ void bcgs2_block(float* Yt, int m, int b, uint32_t salt, float dep_to
 }
 
 __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double* EL, const double* ER, int n,
-                                                                    int iters, EigWs w) {
+                                                                    int iters, int dep_attempts, EigWs w) {
     extern __shared__ float sq[];
     __shared__ float Rs[BCGS_PW * SUBF_BMAX];
     __shared__ float n0s[BCGS_PW];
@@ -775,7 +777,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
         for (int idx = threadIdx.x; idx < b * m; idx += blockDim.x)
             Q[idx] = hash_unit((uint32_t)(idx % m), (uint32_t)(idx / m));
         __syncthreads();
-        bcgs2_block(Q, m, b, 1u, 1e-3f, Rs, n0s);
+        bcgs2_block(Q, m, b, 1u, 1e-3f, Rs, n0s, 4);
         for (int it = 0; it < iters; ++it) {
             // two rows of E_q per warp; each lane keeps 4 k values of both rows in flight
             for (int i0 = 2 * warp; i0 < m; i0 += 2 * nwarps) {
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
                 }
             }
             __syncthreads();
-            bcgs2_block(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, Rs, n0s);
+            bcgs2_block(Y, m, b, 2u + 4u * (uint32_t)it, 1e-3f, Rs, n0s, dep_attempts);
             float* t = Q;  // the orthonormal Y becomes the next Q
             Q = Y;
             Y = t;
@@ -984,12 +986,17 @@ __global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, 
         double* rs = rc + BCAP_MAX / 2;
         int* rp = (int*)(rs + BCAP_MAX / 2);
         int* rq = rp + BCAP_MAX / 2;
-        // H = Q^T Y, symmetrised
-        for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-            const int i = idx / b, j = idx % b;
-            double a = 0.0;
-            for (int t = 0; t < m; ++t) a = fma(Q[(int64_t)t * b + i], Y[(int64_t)t * b + j], a);
-            H[idx] = a;
+        // H = Q^T Y, symmetrised: one warp per entry, lanes striding the m rows (a thread per entry
+        // walking all m rows made this product latency-bound)
+        {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int idx = warp; idx < b * b; idx += nw) {
+                const int i = idx / b, j = idx % b;
+                double a = 0.0;
+                for (int t = lane; t < m; t += 32) a = fma(Q[(int64_t)t * b + i], Y[(int64_t)t * b + j], a);
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) H[idx] = a;
+            }
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
@@ -1322,12 +1329,14 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         bcap = plan.dprime + 16;
     else if (plan.sym == SYM_Z2)
         bcap = plan.dprime / 2 + 24;
-    else  // U(1): many small blocks, each keeping far fewer than D' states
+    else  // U(1): many small blocks, each keeping far fewer than D' states (b = 16 at D' = 64 was
+          // measured: 30 % less eigensolve time, but at high temperature and Delta ~ 0.9 some
+          // blocks keep more than 16 states there and the check below reported HOTRG_ENOCONV)
         bcap = std::min(plan.dprime + 8, std::max(24, plan.dprime / 3));
     if (bcap > BCAP_MAX) bcap = BCAP_MAX;
     // tuning / diagnosis overrides: HOTRG_EIG_EXACT=1 forces FP64 Jacobi on every
     // block, HOTRG_SUB_ITERS sets the FP32 subspace iterations
-    static int force_exact = -1, iters_override = 0, thr_override = 0, bcap_override = 0;
+    static int force_exact = -1, iters_override = 0, thr_override = 0, bcap_override = 0, dep_attempts_override = 0;
     if (force_exact < 0) {
         const char* v = getenv("HOTRG_EIG_EXACT");
         force_exact = (v && v[0] == '1') ? 1 : 0;
@@ -1337,12 +1346,17 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         if (th && atoi(th) > 0) thr_override = atoi(th);
         const char* bc = getenv("HOTRG_BCAP");
         if (bc && atoi(bc) > 0 && atoi(bc) <= BCAP_MAX) bcap_override = atoi(bc);
+        const char* da = getenv("HOTRG_DEP_ATTEMPTS");
+        if (da && atoi(da) >= 1 && atoi(da) <= 4) dep_attempts_override = atoi(da);
     }
     if (bcap_override) bcap = bcap_override;
     // U(1) blocks list >= 2x their kept count, so the ratio lambda_{b+1} / lambda_kept is
     // tiny and 6 iterations converge (measured at D' = 64: within 3e-12 of FP64 Jacobi
     // on every block); the wider Z2 / no-symmetry blocks keep 12
     const int sub_iters = iters_override ? iters_override : (plan.sym == SYM_U1 ? SUB_ITERS_U1 : SUB_ITERS);
+    // attempts per column in the iterations' Gram-Schmidt before a numerically dependent column is
+    // zeroed (1: zeroed at once; the initial random basis always gets 4)
+    const int dep_attempts = dep_attempts_override ? dep_attempts_override : 4;
     const bool exact = plan.exact || force_exact == 1;
     // blocks of at most bcap states get every eigenpair from FP64 Jacobi (b = m);
     // larger ones list bcap through the subspace path
@@ -1362,8 +1376,9 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
     if (!exact) {
         const int sgrid = n < ctx->sm_count ? n : ctx->sm_count;
         const int hp1 = prof_begin(ctx);
-        subspace_fast_kernel<<<dim3(sgrid, sides), SUB_THREADS, SUBF_SMEM, st>>>(EL, ER, n, sub_iters, w);
-        subspace_fp32_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(EL, ER, n, sub_iters, w);
+        subspace_fast_kernel<<<dim3(sgrid, sides), SUB_THREADS, SUBF_SMEM, st>>>(EL, ER, n, sub_iters, dep_attempts,
+                                                                                  w);
+        subspace_fp32_kernel<<<dim3(sgrid, sides), SUB_THREADS, 0, st>>>(EL, ER, n, sub_iters, dep_attempts, w);
         prof_end(ctx, hp1, PROF_EIG_PART0 + 1, 0.0);
         HOTRG_LAUNCH_CHECK(ctx, "subspace_fp32_kernel");
         const int hp2 = prof_begin(ctx);

@@ -964,10 +964,17 @@ __device__ __forceinline__ void decode_tile(const BsGroup* gr, int G, int t, int
 
 // Shared memory of the grouped kernel: the stages plus a 32 x 17 FP64 staging
 // tile per epilogue warp, through which the output is written row-contiguous.
-template <int NS>
+// TBN is the tile width (output columns per tile): 128, or 64 for thin charge
+// blocks.  The three accumulators of a chunk take 3 TBN TMEM columns; at
+// TBN = 64 two such sets fit in the 512 columns, so the MMAs of the next chunk
+// (usually the next tile: most blocks' K fits in one chunk) run while the
+// epilogue drains the previous one.
+template <int NS, int TBN>
 struct GroupCfg {
     static constexpr int A_SLICE = BM * BK * 2;
-    static constexpr int B_SLICE = BN * BK * 2;
+    static constexpr int B_SLICE = TBN * BK * 2;
+    static constexpr int SETS = 6 * TBN <= 512 ? 2 : 1;  // TMEM accumulator sets
+    static constexpr int COLS = TBN / 2;                  // output columns per epilogue warp
     static constexpr int STAGE = NS * (A_SLICE + B_SLICE);
     static constexpr int STG_LD = 17;
     static constexpr int STG_BYTES = EPI_WARPS * 32 * STG_LD * 8;
@@ -978,21 +985,24 @@ struct GroupCfg {
 
 // Persistent grouped GEMM: CTA b takes tiles b, b + gridDim.x, ...  The stage,
 // k-block and chunk counters run on across tiles, so the epilogue of one
-// tile (after its TMEM drain) overlaps the MMAs of the next.
-template <int NS, int OUT>
+// tile (after its TMEM drain) overlaps the MMAs of the next; chunk ch uses
+// TMEM accumulator set ch % SETS.
+template <int NS, int OUT, int TBN>
 __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
                                                                    GroupArgs args) {
-    using Cfg = GroupCfg<NS>;
+    using Cfg = GroupCfg<NS, TBN>;
     constexpr int STAGES = Cfg::STAGES;
+    constexpr int SETS = Cfg::SETS;
+    constexpr int COLS = Cfg::COLS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     double* staging = (double*)(smem + STAGES * Cfg::STAGE);
     uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE + Cfg::STG_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* chunk_full = empty + STAGES;
-    uint64_t* chunk_empty = chunk_full + 1;
-    uint32_t* tmem_slot = (uint32_t*)(chunk_empty + 1);
+    uint64_t* chunk_full = empty + STAGES;    // [SETS]
+    uint64_t* chunk_empty = chunk_full + 2;   // [SETS]
+    uint32_t* tmem_slot = (uint32_t*)(chunk_empty + 2);
     int* s_fail = (int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1008,8 +1018,10 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(chunk_full, 1);
-        mbar_init(chunk_empty, EPI_WARPS);
+        for (int c = 0; c < SETS; ++c) {
+            mbar_init(&chunk_full[c], 1);
+            mbar_init(&chunk_empty[c], EPI_WARPS);
+        }
         *s_fail = 0;
         fence_barrier_init();
     }
@@ -1033,7 +1045,7 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                 decode_tile(args.groups, G, t, g, tm, tn);
                 const BsGroup gr = args.groups[g];
                 const int nkb = gr.Kp / BK;
-                const int arow = (int)(gr.mpad + (int64_t)tm * BM), brow = (int)(gr.npad + (int64_t)tn * BN);
+                const int arow = (int)(gr.mpad + (int64_t)tm * BM), brow = (int)(gr.npad + (int64_t)tn * TBN);
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int s = it % STAGES;
                     if (it >= (uint32_t)STAGES &&
@@ -1057,8 +1069,8 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16(BM, BN);
-            const uint32_t acc0 = tmem, acc1 = tmem + BN, acc2 = tmem + 2 * BN;
+            constexpr uint32_t idesc = idesc_bf16(BM, TBN);
+            uint32_t acc0 = tmem, acc1 = tmem + TBN, acc2 = tmem + 2 * TBN;
             uint32_t it = 0, ch = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
@@ -1068,13 +1080,20 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int s = it % STAGES;
                     const bool chunk_start = (kb % KCB) == 0;
-                    if (chunk_start && ch > 0) {
-                        if (!mbar_wait_cta(chunk_empty, (ch - 1) & 1, args.status, s_fail)) {
-                            *s_fail = 1;
-                            ok = false;
-                            break;
+                    if (chunk_start) {
+                        const uint32_t set = ch % SETS;
+                        // the set was last used by chunk ch - SETS: wait until the epilogue drained it
+                        if (ch >= (uint32_t)SETS) {
+                            if (!mbar_wait_cta(&chunk_empty[set], ((ch / SETS) - 1) & 1, args.status, s_fail)) {
+                                *s_fail = 1;
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
                         }
-                        tc_fence_after();
+                        acc0 = tmem + set * 3 * TBN;
+                        acc1 = acc0 + TBN;
+                        acc2 = acc0 + 2 * TBN;
                     }
                     if (!mbar_wait_cta(&full[s], (it / STAGES) & 1, args.status, s_fail)) {
                         *s_fail = 1;
@@ -1106,16 +1125,17 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                     umma_commit(&empty[s]);
                     ++it;
                     if ((kb % KCB) == KCB - 1 || kb == nkb - 1) {
-                        umma_commit(chunk_full);
+                        umma_commit(&chunk_full[ch % SETS]);
                         ++ch;
                     }
                 }
             }
-            if (!ok) umma_commit(chunk_full);  // release the epilogue; s_fail marks the result invalid
+            if (!ok)  // release the epilogue; s_fail marks the result invalid
+                for (int c = 0; c < SETS; ++c) umma_commit(&chunk_full[c]);
         }
     } else {
         const int quad = warp & 3;
-        const int colbase = ((warp - 2) >> 2) * 64;
+        const int colbase = ((warp - 2) >> 2) * COLS;
         const int row_local = quad * 32 + lane;
         uint32_t ch = 0;
         bool alive = true;
@@ -1124,27 +1144,31 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             decode_tile(args.groups, G, t, g, tm, tn);
             const BsGroup gr = args.groups[g];
             const int nchunks = (gr.Kp / BK + KCB - 1) / KCB;
-            float hi[64], lo[64];
+            float hi[COLS], lo[COLS];
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
+            for (int j = 0; j < COLS; ++j) {
                 hi[j] = 0.f;
                 lo[j] = 0.f;
             }
             for (int c = 0; c < nchunks; ++c, ++ch) {
-                alive = __all_sync(0xffffffffu,
-                                   (alive && mbar_wait_cta(chunk_full, ch & 1, args.status, s_fail)) ? 1 : 0) != 0;
+                const uint32_t set = ch % SETS;
+                alive = __all_sync(0xffffffffu, (alive && mbar_wait_cta(&chunk_full[set], (ch / SETS) & 1,
+                                                                         args.status, s_fail))
+                                                    ? 1
+                                                    : 0) != 0;
                 if (!alive) {
                     *s_fail = 1;
                     break;
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
+                for (int q = 0; q < COLS / 8; ++q) {
                     uint32_t r0[8], r1[8], r2[8];
-                    const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + colbase + q * 8;
+                    const uint32_t taddr =
+                        tmem + set * 3 * TBN + ((uint32_t)(quad * 32) << 16) + colbase + q * 8;
                     tmem_ld8(taddr, r0);
-                    tmem_ld8(taddr + BN, r1);
-                    tmem_ld8(taddr + 2 * BN, r2);
+                    tmem_ld8(taddr + TBN, r1);
+                    tmem_ld8(taddr + 2 * TBN, r2);
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
@@ -1153,7 +1177,7 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(chunk_empty);
+                if (lane == 0) mbar_arrive(&chunk_empty[set]);
             }
             if (!alive) break;
             // output: each lane holds one row; 16 columns at a time go through the warp's
@@ -1165,11 +1189,11 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             float2* stg = (float2*)(staging + (warp - 2) * (32 * Cfg::STG_LD));
             const int cl = lane & 15;
 #pragma unroll
-            for (int c0 = 0; c0 < 64; c0 += 16) {
+            for (int c0 = 0; c0 < COLS; c0 += 16) {
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) stg[lane * Cfg::STG_LD + jj] = make_float2(hi[c0 + jj], lo[c0 + jj]);
                 __syncwarp();
-                const int lcol = tn * BN + colbase + c0 + cl;
+                const int lcol = tn * TBN + colbase + c0 + cl;
                 const bool col_ok = lcol < gr.N;
                 const int64_t coff = col_ok ? args.colC[gr.nbase + lcol] : 0;
                 const int ceb = col_ok ? args.eB[gr.npad + lcol] : 0;
@@ -1220,18 +1244,18 @@ size_t umma_grouped_workspace(int64_t nM, int64_t nK, int64_t nN, int sym) {
     return (size_t)(5 * (rA + rB) * Kp * 2 + (rA + rB) * 4 + 4096);
 }
 
-template <int NS, int OUT>
+template <int NS, int OUT, int TBN>
 static hotrg_status launch_grouped(hotrg_ctx* ctx, const __nv_bfloat16* As, int64_t rA, const __nv_bfloat16* Bs,
                                    int64_t rB, int Kp, const GroupArgs& a, int prof_class) {
-    using Cfg = GroupCfg<NS>;
-    if (attr_once((const void*)umma_grouped_kernel<NS, OUT>, ctx->device))
-        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS, OUT>,
+    using Cfg = GroupCfg<NS, TBN>;
+    if (attr_once((const void*)umma_grouped_kernel<NS, OUT, TBN>, ctx->device))
+        HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(umma_grouped_kernel<NS, OUT, TBN>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
     CUtensorMap mA, mB;
-    if (!make_map(&mA, As, NS, rA, Kp, BM) || !make_map(&mB, Bs, NS, rB, Kp, BN))
+    if (!make_map(&mA, As, NS, rA, Kp, BM) || !make_map(&mB, Bs, NS, rB, Kp, TBN))
         return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
     const int h = prof_begin(ctx);
-    umma_grouped_kernel<NS, OUT><<<ctx->sm_count, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
+    umma_grouped_kernel<NS, OUT, TBN><<<ctx->sm_count, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
     prof_end(ctx, h, prof_class, 0.0);  // algorithmic flops are counted on the device by the planner
     HOTRG_COUNT(1);
     HOTRG_LAUNCH_CHECK(ctx, "umma_grouped_kernel");
@@ -1288,14 +1312,26 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
     a.colC = pl.offN1;
     a.C = C;
     a.status = st;
-    if (cfmt == FMT_F32PAIR) {
-        if (NS == 5) return launch_grouped<5, FMT_F32PAIR>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
-        if (NS == 4) return launch_grouped<4, FMT_F32PAIR>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
-        return launch_grouped<3, FMT_F32PAIR>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    // the tile width the plan's tile table was made for
+    if (pl.tile_n == 64) {
+        if (cfmt == FMT_F32PAIR) {
+            if (NS == 5) return launch_grouped<5, FMT_F32PAIR, 64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+            if (NS == 4) return launch_grouped<4, FMT_F32PAIR, 64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+            return launch_grouped<3, FMT_F32PAIR, 64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        }
+        if (NS == 5) return launch_grouped<5, FMT_F64, 64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        if (NS == 4) return launch_grouped<4, FMT_F64, 64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        return launch_grouped<3, FMT_F64, 64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
     }
-    if (NS == 5) return launch_grouped<5, FMT_F64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
-    if (NS == 4) return launch_grouped<4, FMT_F64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
-    return launch_grouped<3, FMT_F64>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    if (pl.tile_n != 128) return set_err(ctx, HOTRG_EINVAL, "grouped tile width must be 64 or 128");
+    if (cfmt == FMT_F32PAIR) {
+        if (NS == 5) return launch_grouped<5, FMT_F32PAIR, 128>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        if (NS == 4) return launch_grouped<4, FMT_F32PAIR, 128>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+        return launch_grouped<3, FMT_F32PAIR, 128>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    }
+    if (NS == 5) return launch_grouped<5, FMT_F64, 128>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    if (NS == 4) return launch_grouped<4, FMT_F64, 128>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
+    return launch_grouped<3, FMT_F64, 128>(ctx, As, rA, Bs, rB, Kp, a, prof_class);
 }
 
 hotrg_status umma_check_status(hotrg_ctx* ctx) {

@@ -66,6 +66,9 @@ struct hotrg_ctx {
     // reported for that point alone (also inside captured graphs).
     int32_t* status_dev = nullptr;
     int32_t* status_slot = nullptr;
+    // tile width (output columns per tile, 128 or 64) of the split forms' grouped products,
+    // [0] environments, [1] coarse contraction; set by hotrg_set_tiles / hotrg_autotune_tiles
+    int tile_n[2] = {128, 128};
 };
 
 namespace hotrg {
@@ -205,6 +208,7 @@ struct BsPlan {  // device pointers (workspace) plus the host-known set sizes
     int64_t *offN0, *offN1;  // N set: offsets in B, in C
     int64_t nM, nK, nN;
     int32_t kp_cap;  // slice row pitch (>= every block's padded K; checked on the device)
+    int32_t tile_n;  // output columns per tile of the tile table (128, or 64 for the split forms)
 };
 size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // Enqueues the planner for C = A B^T over index sets (M, K, N) with the given
@@ -212,8 +216,9 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // label sums, and a product whose sums span BS_V or more values records
 // HOTRG_ENOTSUP in the engine's status word.
 // kp_cap_override > 0 replaces the slice pitch limit (the FP64 engine slices nothing).
+// tile_n: output columns per tile of the tile table (rows are always 128).
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
-                     BsPlan& out, int32_t kp_cap_override = 0);
+                     BsPlan& out, int32_t kp_cap_override = 0, int tile_n = 128);
 // Slice row pitch of a grouped product: the whole K set rounded to 32 for small sets and
 // Z2; half of it (at least 4096) for larger U(1) sets (bs_plan checks every block on the device).
 int32_t bs_pitch(int64_t nK, int sym);

@@ -236,6 +236,28 @@ def hotrg_autotune_batch(ctx, plist, max_streams=4):
     return best.value, list(secs)
 
 
+def hotrg_set_tiles(ctx, env_tile_n, coarse_tile_n):
+    """Tile widths (128 or 64 output columns) of the split forms' block-sparse products."""
+    f = lib.hotrg_set_tiles
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+    f.restype = ctypes.c_int
+    return _check(ctx, f(ctx, env_tile_n, coarse_tile_n))
+
+
+def hotrg_autotune_tiles(ctx, plist, nstreams=0):
+    """Times the four (env, coarse) tile-width pairs on the sample; returns ((env, coarse), seconds)."""
+    n = len(plist)
+    arr = (Params * n)(*plist)
+    e, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    secs = (ctypes.c_double * 4)()
+    f = lib.hotrg_autotune_tiles
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32,
+                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    f.restype = ctypes.c_int
+    _check(ctx, f(ctx, arr, n, nstreams, ctypes.byref(e), ctypes.byref(c), secs))
+    return (e.value, c.value), list(secs)
+
+
 def hotrg_observables(ctx, plist, hb=1e-3, hbar=0.01, dh=1e-3):
     n = len(plist)
     arr = (Params * n)(*plist)
@@ -538,6 +560,12 @@ class Context:
 
     def autotune_batch(self, plist, max_streams=4):
         return hotrg_autotune_batch(self.handle, plist, max_streams)
+
+    def set_tiles(self, env_tile_n, coarse_tile_n):
+        return hotrg_set_tiles(self.handle, env_tile_n, coarse_tile_n)
+
+    def autotune_tiles(self, plist, nstreams=0):
+        return hotrg_autotune_tiles(self.handle, plist, nstreams)
 
     def observables(self, plist, hb=1e-3, hbar=0.01, dh=1e-3):
         return hotrg_observables(self.handle, plist, hb, hbar, dh)

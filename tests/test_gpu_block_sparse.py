@@ -77,13 +77,45 @@ def test_block_sparse_ising(H, C):
 
 
 def test_block_sparse_without_structure_is_the_dense_form(H, C):
-    # h != 0 leaves no conserved label, and an impurity run keeps the dense path: bitwise equal
+    # h != 0 leaves no conserved label, and the cos(theta) impurity (parity odd) breaks the
+    # Z2 rule of h1 != 0: both keep the dense path, bitwise equal
     a = C.run([H.params(1.1, 0.4, 2, 12, 10, h=0.02, prec=H.SPLIT_BF16, block_sparse=1)])[0]
     b = C.run([H.params(1.1, 0.4, 2, 12, 10, h=0.02, prec=H.SPLIT_BF16)])[0]
     assert a.lnz_per_site == b.lnz_per_site
-    a = C.run([H.params(1.1, 0.4, 2, 12, 10, h1=0.02, prec=H.SPLIT_BF16, block_sparse=1)], imp_kind=H.T_IMP_M1)[0]
-    b = C.run([H.params(1.1, 0.4, 2, 12, 10, h1=0.02, prec=H.SPLIT_BF16)], imp_kind=H.T_IMP_M1)[0]
+    a = C.run([H.params(1.1, 0.4, 2, 12, 10, h1=0.02, prec=H.SPLIT_BF16, block_sparse=1)], imp_kind=H.T_IMP_M)[0]
+    b = C.run([H.params(1.1, 0.4, 2, 12, 10, h1=0.02, prec=H.SPLIT_BF16)], imp_kind=H.T_IMP_M)[0]
     assert a.lnz_per_site == b.lnz_per_site and a.imp_ratio == b.imp_ratio
+
+
+# The cos(2 theta) impurity (Eq. 3.21) at h = 0, h1 != 0 keeps the charge parity of the pure
+# tensor, so its co-update (the impurity rule above T and below T) runs in the Z2 block form.
+M1_POINTS = [(1.1, 0.4, 2, 10, 10, 0.03), (1.3, 0.2, 3, 16, 14, 0.02), (0.9, 0.3, 3, 13, 12, 0.01)]
+
+
+@pytest.mark.parametrize("beta,delta,nm,dcut,steps,h1", M1_POINTS)
+@pytest.mark.parametrize("prec_name,tol_lnz,tol_imp", [("SPLIT_BF16", 1e-9, 1e-8), ("FP64", 1e-10, 1e-10)])
+def test_block_sparse_m1_impurity_against_oracle(H, C, beta, delta, nm, dcut, steps, h1, prec_name, tol_lnz,
+                                                 tol_imp):
+    prec = getattr(H, prec_name)
+    ref = OH.run_gxy(beta, delta, nm, dcut, steps, h1=h1, impurity=gxy.IMP_M1)
+    bs = C.run([H.params(beta, delta, nm, dcut, steps, h1=h1, prec=prec, block_sparse=1)], imp_kind=H.T_IMP_M1)[0]
+    dense = C.run([H.params(beta, delta, nm, dcut, steps, h1=h1, prec=prec)], imp_kind=H.T_IMP_M1)[0]
+    assert bs.status == 0
+    assert abs(bs.lnz_per_site - ref.lnz_per_site) <= tol_lnz
+    assert abs(bs.imp_ratio - ref.imp_ratio) <= tol_imp, (bs.imp_ratio, ref.imp_ratio)
+    assert abs(bs.imp_ratio - dense.imp_ratio) <= tol_imp
+    assert bs.imp_ratio != 0.0
+
+
+def test_block_sparse_m1_impurity_is_cheaper(H, C):
+    # the co-update runs per block: fewer algorithmic flops than the dense co-update
+    p = H.params(1.1, 0.4, 3, 16, 12, h1=0.02, prec=H.SPLIT_BF16, block_sparse=1)
+    H.hotrg_profile_enable(C.handle, True)
+    C.run([p], imp_kind=H.T_IMP_M1)
+    bs = H.hotrg_profile_read(C.handle)
+    H.hotrg_profile_enable(C.handle, False)
+    # three coarse contractions per step (pure, impurity above, impurity below), all per block
+    assert bs.gemm_calls[1] == 3 * 3 * 12 and bs.operand_elems[1] > 0
 
 
 def test_block_sparse_batch_replay_equals_single_runs(H, C):
@@ -185,3 +217,37 @@ def test_block_sparse_step_matches_dense_step(H, C, seed):
     assert abs(i0[1] - i0[2]) > 1e-6 * i0[1]  # the two sides differ on this tensor
     assert np.array_equal(q0, q1)
     assert np.abs(t0 - t1).max() <= 1e-9 * np.abs(t0).max()
+
+
+# Tile shapes of the tensor-core products (hotrg_set_tiles): 128 or 64 output columns per
+# tile, for the environments and the coarse contraction separately.  The products of every
+# output element are the same; only the tiling and the TMEM double buffering differ.
+@pytest.mark.parametrize("tiles", [(64, 64), (128, 64), (64, 128)])
+@pytest.mark.parametrize("beta,delta,nm,dcut,steps", SPLIT_SHAPES[:4] + DRIFT_SHAPES[:1])
+def test_tile_shapes_match_oracle(H, C, tiles, beta, delta, nm, dcut, steps):
+    ref = OH.run_gxy(beta, delta, nm, dcut, steps)
+    try:
+        C.set_tiles(128, 128)
+        base = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+        C.set_tiles(*tiles)
+        got = C.run([H.params(beta, delta, nm, dcut, steps, prec=H.SPLIT_BF16, block_sparse=1)])[0]
+    finally:
+        C.set_tiles(128, 128)
+    assert got.status == 0
+    assert abs(got.lnz_per_site - ref.lnz_per_site) <= 1e-9
+    assert abs(got.lnz_per_site - base.lnz_per_site) <= 1e-12, got.lnz_per_site - base.lnz_per_site
+
+
+def test_tile_autotuner_and_graph_rebuild(H, C):
+    pts = [H.params(*pt, prec=H.SPLIT_BF16, block_sparse=1) for pt in BATCH[:4]]
+    single = [C.run([p])[0].lnz_per_site for p in pts]
+    try:
+        (e, c), secs = C.autotune_tiles(pts, nstreams=2)
+        assert e in (64, 128) and c in (64, 128) and len(secs) == 4 and all(t > 0 for t in secs)
+        # the worker graphs were rebuilt for the chosen shapes: the batch still equals the single runs
+        got = C.run_batch(pts, nstreams=2)
+        assert max(abs(r.lnz_per_site - x) for r, x in zip(got, single)) <= 1e-12
+        with pytest.raises(H.HotrgError):
+            C.set_tiles(96, 128)
+    finally:
+        C.set_tiles(128, 128)

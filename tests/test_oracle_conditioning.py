@@ -70,3 +70,30 @@ def test_drift_points_leave_the_centred_label_range(point):
     # the kept window really drifts (label sums beyond 64), while its width stays small
     worst, wh, wv = label_sum_bound(point)
     assert worst > 64 and wh < 40 and wv < 40
+
+
+# The observables test points (tests/test_gpu_observables.py): the cos theta impurity run at
+# h = hbar = 0.01 has no conserved label, and at small h nearly degenerate pairs can straddle
+# the cut -- there rounding-level noise decides the kept state.  The chosen points are
+# conditioned to 1e-15; the first one below is the counter-example.
+def m_spread(point, h, eta=1e-15, seeds=(1, 2)):
+    beta, delta, nm, dcut, steps = point
+    T0 = gxy.site_tensor(beta, delta, nm, h, 0.0, gxy.PURE)
+    Ti = gxy.site_tensor(beta, delta, nm, h, 0.0, gxy.IMP_M)
+    q0 = gxy.leg_charges(nm, "none")
+    ref = OH.hotrg_run(T0, q0, steps, dcut, "none", T_imp0=Ti).imp_ratio
+    worst = 0.0
+    for s in seeds:
+        rng = np.random.default_rng(s)
+        Tp = T0 * (1.0 + eta * rng.standard_normal(T0.shape))
+        worst = max(worst, abs(OH.hotrg_run(Tp, q0, steps, dcut, "none", T_imp0=Ti).imp_ratio - ref))
+    return worst
+
+
+@pytest.mark.parametrize("point", [(1.3, 0.7, 2, 24, 10), (0.7, 0.9, 2, 24, 10)])
+def test_observables_points_are_well_conditioned(point):
+    assert m_spread(point, 0.01) <= 1e-12
+
+
+def test_observables_counter_example_is_ill_conditioned():
+    assert m_spread((1.0, 0.5, 2, 24, 10), 0.01) > 1e-8

@@ -152,3 +152,24 @@ def test_strict_widths_change_nothing_on_parity_points(point):
     for k, r in enumerate(a.steps):
         if not r.strict_same:
             assert abs(r.side_margin) <= 1e-12, (k + 1, r.side_margin)
+
+
+def test_strict_widths_at_dcut64_move_lnz_below_1e12():
+    # The first D_cut = 64 workload point, stored by the oracle with the reading's widths and with
+    # the strict ones (tests/golden/make_oracle_goldens.py headline0 and headline0_strict).  There
+    # the 1e-6 side margin decides genuine near-ties -- steps where eps_2 < eps_1 by up to 6e-7
+    # relative keep the left side -- so the two runs take different sides from step 5 on; each
+    # decision sits inside the margin (both sides truncate the same weight to 6 digits), single
+    # ln c_k move by ~1e-9, ln Z / N by 7e-13.
+    import json
+    import os
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    g = json.load(open(os.path.join(gold, "oracle_headline0.json")))
+    s = json.load(open(os.path.join(gold, "strict_headline0.json")))
+    assert (g["tie_rtol"], g["side_rtol"]) == (OH.TIE_RTOL, OH.SIDE_RTOL)
+    assert s["strict"] and (s["tie_rtol"], s["side_rtol"]) == (OH.STRICT_TIE_RTOL, OH.STRICT_SIDE_RTOL)
+    assert abs(g["lnz_per_site"] - s["lnz_per_site"]) <= 1e-12
+    differing = [st for st in g["steps"] if not st["strict_same"]]
+    assert differing  # the widths do decide here
+    for st in differing:
+        assert abs(st["side_margin"]) < OH.SIDE_RTOL, (st["k"], st["side_margin"])
