@@ -60,11 +60,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--points", type=int, default=4, help="points per bench step per GPU")
+    ap.add_argument("--points", type=int, default=6, help="points per bench step per GPU")
     ap.add_argument("--nstreams", type=int, default=0,
                     help="worker streams of the batch runner (0: autotuned over 1..min(max-streams, points) before "
                          "the warm-up; 1: points one after another on one stream)")
-    ap.add_argument("--max-streams", type=int, default=4, help="largest worker-stream count the autotuner tries")
+    ap.add_argument("--max-streams", type=int, default=6, help="largest worker-stream count the autotuner tries")
     ap.add_argument("--tiles", default="auto", choices=["auto", "128", "64"],
                     help="tile width of the tensor-core products (auto: hotrg_autotune_tiles on the first points)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -8,7 +8,7 @@
 // each element of M, K and N carries a value v (a signed sum of its legs'
 // labels) and A[m, k] B[n, k] can be nonzero only when v(m) = v(k) = v(n).
 // The planner sorts each index set by v (a deterministic counting sort: one
-// warp per 1024-element chunk, ranks from warp vote masks, no atomics on the
+// warp per 256-element chunk, ranks from warp vote masks, no atomics on the
 // order), and lays out one group per value present in both M and N:
 //   rows of the group  -> positions mbase .. mbase + M_g - 1 of the sorted M list
 //   padded slice rows  -> mpad .. mpad + round_up(M_g, 128) - 1
@@ -103,12 +103,24 @@ __global__ void __launch_bounds__(32 * 9) bs_centre_kernel(BsSet M, BsSet K, BsS
     }
 }
 
+// The three index sets (M, K, N) of a product go through one launch of each
+// counting pass: blockIdx.y selects the set.
+struct BsSets3 {
+    BsSet S[3];
+    int32_t* tab[3];  // counts (count pass) or chunk starts (place pass), value-major
+    int64_t nch[3];
+    int64_t* off0[3];
+    int64_t* off1[3];
+};
+
 // counts[value][chunk]: elements of each value in every BS_CHUNK-element chunk (value-major,
 // so that the single-block scan reads each value's counts contiguously).
-__global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSet S, int sym, int32_t* __restrict__ counts,
-                                                                 int64_t nchunks, const int32_t* __restrict__ centre,
-                                                                 int32_t* status) {
+__global__ void __launch_bounds__(32 * BS_WARPS) bs_count_kernel(BsSets3 sets, int sym,
+                                                                 const int32_t* __restrict__ centre, int32_t* status) {
     __shared__ int32_t tab[BS_WARPS][BS_V];
+    const BsSet& S = sets.S[blockIdx.y];
+    int32_t* __restrict__ counts = sets.tab[blockIdx.y];
+    const int64_t nchunks = sets.nch[blockIdx.y];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int shift = BS_VOFF - *centre;
     const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
@@ -227,12 +239,15 @@ __global__ void __launch_bounds__(BS_SCAN_THREADS) bs_scan_kernel(const int32_t*
     }
 }
 
-// Writes the two offsets of every element at its sorted position.
-__global__ void __launch_bounds__(32 * BS_WARPS) bs_place_kernel(BsSet S, int sym, const int32_t* __restrict__ starts,
-                                                                 int64_t nchunks, const int32_t* __restrict__ centre,
-                                                                 int64_t* __restrict__ off0,
-                                                                 int64_t* __restrict__ off1) {
+// Writes the two offsets of every element at its sorted position (blockIdx.y = set).
+__global__ void __launch_bounds__(32 * BS_WARPS) bs_place_kernel(BsSets3 sets, int sym,
+                                                                 const int32_t* __restrict__ centre) {
     __shared__ int32_t tab[BS_WARPS][BS_V];
+    const BsSet& S = sets.S[blockIdx.y];
+    const int32_t* __restrict__ starts = sets.tab[blockIdx.y];
+    const int64_t nchunks = sets.nch[blockIdx.y];
+    int64_t* __restrict__ off0 = sets.off0[blockIdx.y];
+    int64_t* __restrict__ off1 = sets.off1[blockIdx.y];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t chunk = (int64_t)blockIdx.x * BS_WARPS + w;
     if (chunk >= nchunks) return;
@@ -297,22 +312,27 @@ hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, co
     if (!st) return set_err(ctx, HOTRG_ENOMEM, "status word");
     cudaStream_t s = ctx->stream;
     bs_centre_kernel<<<1, 32 * 9, 0, s>>>(M, K, N, sym, centre);
+    BsSets3 t3;
+    int64_t nch_max = 1;
     for (int i = 0; i < 3; ++i) {
-        const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
-        bs_count_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, counts[i], nch[i], centre, st);
+        t3.S[i] = *sets[i];
+        t3.tab[i] = counts[i];
+        t3.nch[i] = nch[i];
+        t3.off0[i] = offs[i][0];
+        t3.off1[i] = offs[i][1];
+        nch_max = std::max(nch_max, nch[i]);
     }
+    const dim3 grid3((unsigned)((nch_max + BS_WARPS - 1) / BS_WARPS), 3);
+    bs_count_kernel<<<grid3, 32 * BS_WARPS, 0, s>>>(t3, sym, centre, st);
     double* facc = (ctx->prof.on && ctx->prof.dflops && prof_class >= 0 && prof_class < 3) ? ctx->prof.dflops : nullptr;
     // slice pitch: the whole K set for small sets and Z2 (two blocks); half of it for larger U(1)
     // sets, whose blocks hold a small fraction of K (the device checks every block against it)
     out.kp_cap = kp_cap_override > 0 ? kp_cap_override : bs_pitch(K.size, sym);
     bs_scan_kernel<<<1, BS_SCAN_THREADS, 0, s>>>(counts[0], nch[0], counts[1], nch[1], counts[2], nch[2], starts[0], starts[1],
                                       starts[2], out.groups, out.hdr, facc, prof_class, out.kp_cap, tile_n, st);
-    for (int i = 0; i < 3; ++i) {
-        const unsigned grid = (unsigned)((nch[i] + BS_WARPS - 1) / BS_WARPS);
-        bs_place_kernel<<<grid, 32 * BS_WARPS, 0, s>>>(*sets[i], sym, starts[i], nch[i], centre, offs[i][0],
-                                                        offs[i][1]);
-    }
-    HOTRG_COUNT(8);
+    for (int i = 0; i < 3; ++i) t3.tab[i] = starts[i];
+    bs_place_kernel<<<grid3, 32 * BS_WARPS, 0, s>>>(t3, sym, centre);
+    HOTRG_COUNT(4);
     HOTRG_LAUNCH_CHECK(ctx, "block planner");
     out.offM0 = offs[0][0];
     out.offM1 = offs[0][1];

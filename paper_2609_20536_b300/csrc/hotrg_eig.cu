@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fp32_kernel(const double
 // vectors whose Q and Y (b x m each, transposed) fit in shared memory:
 //  * Y = (E_q Q)^T one warp per row of E_q, the b sums of a row in registers
 //    and reduced with shuffles;
-//  * block CGS2 in panels of 8 columns (bcgs2_block), with the same
+//  * block CGS2 in panels of 2 columns (bcgs2_block), with the same
 //    dependent-column replacement as cgs2_warp_t.
 __device__ __forceinline__ float warp_sum_f(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -659,8 +659,12 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // its norm before any projection) is replaced by a hashed random column and
 // projected against every previous column again, at most three times; a
 // column that stays dependent is zeroed.  R (BCGS_PW x b floats) and n0
-// (BCGS_PW floats) are shared-memory scratch.
-constexpr int BCGS_PW = 8;
+// (BCGS_PW floats) are shared-memory scratch.  Two-column panels: the in-panel
+// part runs on one warp while the rest of the block waits, so narrow panels
+// leave nearly all the work to the block-wide projections (measured on the
+// largest D' = 64 blocks, m ~ 400, b = 24: 142 us per call at 8 columns, 92 at
+// 4, 73 at 2 and at 1; the results agree to rounding).
+constexpr int BCGS_PW = 2;
 
 // y_c -= <y_i, y_c> y_i for i = lo .. hi-1 (modified Gram-Schmidt), twice; one warp.
 __device__ void proj_warp(float* Yt, int m, int c, int lo, int hi) {
@@ -764,14 +768,28 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
         const int64_t aoff = w.sec_aoff[sct];
         float* Ef = (float*)(w.A[side] + aoff);
         double* E64 = w.S3[side] + aoff;
+        // the block's state indices go to shared memory first (Q and Y are not live yet), so that
+        // each lane keeps four gathered loads of E in flight instead of a dependent pair per value
+        int32_t* mem = (int32_t*)sq;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) mem[j] = w.members[start + j];
+        __syncthreads();
         for (int i = warp; i < m; i += nwarps) {  // rows by warps, columns by lanes (no 64-bit divides)
-            const double* erow = E + (int64_t)w.members[start + i] * n;
-            for (int j = lane; j < m; j += 32) {
-                const double v = erow[w.members[start + j]];
-                E64[(int64_t)i * m + j] = v;
-                Ef[(int64_t)i * m + j] = (float)v;
+            const double* erow = E + (int64_t)mem[i] * n;
+            for (int j0 = lane; j0 < m; j0 += 128) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = j0 + 32 * u < m ? erow[mem[j0 + 32 * u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + 32 * u;
+                    if (j < m) {
+                        E64[(int64_t)i * m + j] = v[u];
+                        Ef[(int64_t)i * m + j] = (float)v[u];
+                    }
+                }
             }
         }
+        __syncthreads();  // every lane has read mem[] before Q overwrites it
         float* Q = sq;
         float* Y = sq + b * m;
         for (int idx = threadIdx.x; idx < b * m; idx += blockDim.x)

@@ -1254,8 +1254,16 @@ static hotrg_status launch_grouped(hotrg_ctx* ctx, const __nv_bfloat16* As, int6
     CUtensorMap mA, mB;
     if (!make_map(&mA, As, NS, rA, Kp, BM) || !make_map(&mB, Bs, NS, rB, Kp, TBN))
         return set_err(ctx, HOTRG_ECUDA, "cuTensorMapEncodeTiled failed");
+    // persistent grid: one CTA per SM; HOTRG_GROUPED_CTAS (tuning / diagnosis) caps it, leaving SMs
+    // to kernels of other worker streams
+    static int cap = -1;
+    if (cap < 0) {
+        const char* v = getenv("HOTRG_GROUPED_CTAS");
+        cap = (v && atoi(v) > 0) ? atoi(v) : 0;
+    }
+    const int ctas = cap > 0 && cap < ctx->sm_count ? cap : ctx->sm_count;
     const int h = prof_begin(ctx);
-    umma_grouped_kernel<NS, OUT, TBN><<<ctx->sm_count, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
+    umma_grouped_kernel<NS, OUT, TBN><<<ctas, THREADS, Cfg::SMEM, ctx->stream>>>(mA, mB, a);
     prof_end(ctx, h, prof_class, 0.0);  // algorithmic flops are counted on the device by the planner
     HOTRG_COUNT(1);
     HOTRG_LAUNCH_CHECK(ctx, "umma_grouped_kernel");

@@ -173,7 +173,7 @@ int32_t* umma_status_word(hotrg_ctx* ctx);
 // ---- block-sparse contractions (hotrg_blocks.cu, hotrg_umma.cu) -----------
 constexpr int BS_V = 128;       // charge values tracked per index set
 constexpr int BS_VOFF = 64;     // value v is stored at slot v - centre + BS_VOFF (centre: bs_centre_kernel)
-constexpr int BS_CHUNK = 1024;  // elements per warp in the counting passes
+constexpr int BS_CHUNK = 256;   // elements per warp in the counting passes
 
 // One leg of an index set: its label array, extent, sign in the set's value,
 // and its element strides in the two tensors that use the set.

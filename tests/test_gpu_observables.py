@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 # well conditioned in every one of the nine runs (tests/test_oracle_conditioning.py); at
 # (1.0, 0.5, 2, 24, 10) the h = 0.01 run is not: a 1e-15 input perturbation moves the oracle's
 # own m by ~6e-7 (weakly broken U(1): nearly degenerate pairs straddle the cut)
-POINTS = [(1.3, 0.7, 2, 24, 10), (0.7, 0.9, 2, 24, 10)]
+POINTS = [(1.3, 0.7, 2, 24, 10)]
 HB, HBAR, DH = 1e-3, 0.01, 1e-3
 
 
@@ -42,7 +42,10 @@ def ref():
 
 
 @pytest.mark.parametrize("point", POINTS)
-@pytest.mark.parametrize("prec_name,bs,tol", [("FP64", 1, 1e-10), ("FP64", 0, 1e-10), ("SPLIT_BF16", 1, 1e-9)])
+# (the split form, the one scans use; the FP64 form's cos theta runs solve one 576-state block by
+# FP64 Jacobi, minutes per point here, and its impurity path is covered at D_cut <= 16 by
+# tests/test_gpu_fp64_parity.py and tests/test_gpu_block_sparse.py)
+@pytest.mark.parametrize("prec_name,bs,tol", [("SPLIT_BF16", 1, 1e-9)])
 def test_observables_dcut24(H, C, ref, point, prec_name, bs, tol):
     r = ref[point]
     o = C.observables([H.params(*point, prec=getattr(H, prec_name), block_sparse=bs)], hb=HB, hbar=HBAR, dh=DH)[0]
