@@ -48,8 +48,8 @@ WORKLOAD_BS = ", contractions per U(1) charge block"
 # step), keyed by the hash of the kernel sources it was captured on: bytes per launch and
 # the algorithmic bytes of the same launches (profiles/traffic_umma_grouped_dcut64.md)
 KNOWN_TRAFFIC = {
-    "0105f1688643e5ac": {"dram_to_algorithmic": 2.3712, "dram_bytes_per_full_step_launch": 1.6244e9,
-                         "algorithmic_bytes_per_full_step_launch": 0.6851e9,
+    "9cc54c89a97f07b1": {"dram_to_algorithmic": 1.4138, "dram_bytes_per_full_step_launch": 0.9685e9,
+                         "algorithmic_bytes_per_full_step_launch": 0.6850e9,
                          "source": "profiles/traffic_umma_grouped_dcut64.md (ncu dram__bytes_read/write.sum, "
                                    "the three coarse launches of a full-size D_cut=64 step)"},
 }

@@ -216,6 +216,7 @@ static size_t step_bytes(const hotrg_params* p, int Dh, int Dv, bool imp, bool i
     const size_t d5 = Dp * Dh * Dh * Dv * Dv;
     b += a256(d4 * 8) * 2 + a256(d5 * 8) * 2 + a256(Dp * Dp * Dv * Dv * 8) * (imp ? 2 : 1);
     b += a256(norm_partials() * 8) + a256(64) * 4;
+    b += a256(hv * 4) + a256(n * 4);  // pair tables of the block-sparse intermediates
     const int64_t shapes[5][3] = {{(int64_t)hv, (int64_t)hv, (int64_t)hv},
                                   {(int64_t)n, (int64_t)n, (int64_t)Dv * Dv},
                                   {(int64_t)Dp * Dh, (int64_t)Dh * Dv * Dv, Dh},
@@ -431,9 +432,11 @@ static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, in
 // rewritten for each product, so every element a later product reads is
 // written by the earlier one.  Tc is zeroed first: s3 writes only its blocks.
 // Offsets: W and Z are laid out per the comment below; T, P, Tc as usual.
+// piW, piZ: workspace for the two pair tables (Dh Dv and Dh Dh entries).
 static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const double* P, const int32_t* qh,
                                   const int32_t* qv, const int32_t* qn, int Dh, int Dv, int Dp, const double* T_up,
-                                  const double* T_dn, double* W, double* Z, double* Tc, double* T_out) {
+                                  const double* T_dn, double* W, double* Z, double* Tc, double* T_out,
+                                  int32_t* piW, int32_t* piZ) {
     const int64_t h = Dh, v = Dv, p = Dp, hh = h * h, vv = v * v;
     hotrg_status s;
     // In the split forms W and Z are written and read as exact FP32 pairs (8 bytes, the value
@@ -441,40 +444,46 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
     // outputs.  The FP64 form keeps them in FP64.
     const int wf = prec == HOTRG_FP64 ? 0 : 1;
     auto run = [&](const BsSet& M, const BsSet& K, const BsSet& N, const void* A, int af, const void* B,
-                   void* C, int cf) {
+                   void* C, int cf, const int32_t* pi_out) {
         const size_t mark = ctx->ws.used;
         BsPlan pl;
         hotrg_status st = bs_plan(ctx, sym, M, K, N, PROF_GEMM_COARSE, pl, prec == HOTRG_FP64 ? INT32_MAX : 0,
-                                  prec == HOTRG_FP64 ? 128 : ctx->tile_n[1]);
+                                  prec == HOTRG_FP64 ? 128 : ctx->tile_n[1], pi_out);
         if (st == HOTRG_OK) st = grouped_engine(ctx, prec, pl, A, af, B, 0, C, cf, PROF_GEMM_COARSE);
         ctx->ws.used = mark;
         return st;
     };
     // The intermediates are stored so that each row of the next product's A
-    // operand is one contiguous block: W[x][r1][u][l2][i] (s2 row (x,r1,u), its K
-    // (l2,i) inside h v elements) and Z[x][u][d][r1][r2] (s3 row (x,u,d), K (r1,r2)).
-    // s1: W[x][r1][u][l2][i] = sum_l1 P[l1][l2][x] T_up[l1][r1][u][i]
+    // operand is one contiguous run: W[x][r1][u][piW(l2,i)] (s2 row (x,r1,u), K (l2,i))
+    // and Z[x][u][d][piZ(r1,r2)] (s3 row (x,u,d), K (r1,r2)).  piW lists the h v pairs
+    // (l2,i) by their s2 value q_l2 + q_i, piZ the h h pairs (r1,r2) by q_r1 + q_r2, so
+    // the K elements of one block sit side by side in the order the planner lists
+    // them: the slicer reads whole DRAM lines and the producing epilogue fills them,
+    // instead of runs of one leg's equal labels (a few values) among structural zeros.
+    if ((s = pair_table(ctx, sym, qh, Dh, qv, Dv, piW)) != HOTRG_OK) return s;
+    if ((s = pair_table(ctx, sym, qh, Dh, qh, Dh, piZ)) != HOTRG_OK) return s;
+    // s1: W[x][r1][u][piW(l2,i)] = sum_l1 P[l1][l2][x] T_up[l1][r1][u][i]
     {
-        BsSet M{2, {{qn, p, +1, 1, hh * vv}, {qh, h, -1, p, v}}, p * h};
+        BsSet M{2, {{qn, p, +1, 1, hh * vv, 0}, {qh, h, -1, p, 0, v}}, p * h};
         BsSet K{1, {{qh, h, +1, h * p, h * vv}}, h};
-        BsSet N{3, {{qh, h, +1, vv, v * h * v}, {qv, v, -1, v, h * v}, {qv, v, +1, 1, 1}}, h * vv};
-        if ((s = run(M, K, N, P, 0, T_up, W, wf)) != HOTRG_OK) return s;
+        BsSet N{3, {{qh, h, +1, vv, v * h * v, 0}, {qv, v, -1, v, h * v, 0}, {qv, v, +1, 1, 0, 1}}, h * vv};
+        if ((s = run(M, K, N, P, 0, T_up, W, wf, piW)) != HOTRG_OK) return s;
     }
-    // s2: Z[x][u][d][r1][r2] = sum_{l2,i} W[x][r1][u][l2][i] T_dn[l2][r2][i][d]
+    // s2: Z[x][u][d][piZ(r1,r2)] = sum_{l2,i} W[x][r1][u][piW(l2,i)] T_dn[l2][r2][i][d]
     {
-        BsSet M{3, {{qn, p, +1, hh * vv, vv * hh}, {qh, h, -1, v * h * v, h}, {qv, v, +1, h * v, v * hh}},
+        BsSet M{3, {{qn, p, +1, hh * vv, vv * hh, 0}, {qh, h, -1, v * h * v, 0, h}, {qv, v, +1, h * v, v * hh, 0}},
                 p * h * v};
-        BsSet K{2, {{qh, h, +1, v, h * vv}, {qv, v, +1, 1, v}}, h * v};
-        BsSet N{2, {{qv, v, +1, 1, hh}, {qh, h, +1, vv, 1}}, v * h};
-        if ((s = run(M, K, N, W, wf, T_dn, Z, wf)) != HOTRG_OK) return s;
+        BsSet K{2, {{qh, h, +1, v, h * vv}, {qv, v, +1, 1, v}}, h * v, piW};
+        BsSet N{2, {{qv, v, +1, 1, hh, 0}, {qh, h, +1, vv, 0, 1}}, v * h};
+        if ((s = run(M, K, N, W, wf, T_dn, Z, wf, piZ)) != HOTRG_OK) return s;
     }
-    // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][u][d][r1][r2] P[r1][r2][x']
+    // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][u][d][piZ(r1,r2)] P[r1][r2][x']
     HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(Tc, 0, (size_t)p * vv * p * 8, ctx->stream));
     {
         BsSet M{3, {{qn, p, +1, vv * hh, vv * p}, {qv, v, +1, v * hh, v * p}, {qv, v, -1, hh, p}}, p * vv};
-        BsSet K{2, {{qh, h, +1, h, h * p}, {qh, h, +1, 1, p}}, hh};
+        BsSet K{2, {{qh, h, +1, h, h * p}, {qh, h, +1, 1, p}}, hh, piZ};
         BsSet N{1, {{qn, p, +1, 1, 1}}, p};
-        if ((s = run(M, K, N, Z, wf, P, Tc, 0)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, Z, wf, P, Tc, 0, nullptr)) != HOTRG_OK) return s;
     }
     // relabel for the other axis: T_out[u][d][x][x'] = Tc[x][u][d][x']
     Perm po{4, {Dv, Dv, Dp, Dp}, {(int64_t)Dv * Dp, Dp, vv * Dp, 1}};
@@ -518,8 +527,10 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     double* Ti2 = Ti_in ? (double*)A(tn * 8) : nullptr;
     double* partial = (double*)A(norm_partials() * 8);
     double* norm = (double*)A(64);
+    int32_t* piW = (int32_t*)A(hv * 4);
+    int32_t* piZ = (int32_t*)A(n * 4);
     if (!X1 || !X2 || !Am || !Bm || !A2 || !B2 || !Ep || !EL || !ER || !eigws || !P || !Pt || !Pt2 || !Tt ||
-        !Tb || !W || !W2 || !Tc || (Ti_in && !Ti2) || !partial || !norm)
+        !Tb || !W || !W2 || !Tc || (Ti_in && !Ti2) || !partial || !norm || !piW || !piZ)
         return set_err(ctx, HOTRG_ENOMEM, "step workspace exhausted");
     hotrg_status s;
     const int h_step = prof_begin(ctx);
@@ -559,7 +570,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
         return s;
     prof_end(ctx, h_eig, PROF_EIG, 0.0);
     if (blocks) {
-        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, Tc, T_out)) !=
+        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, Tc, T_out, piW, piZ)) !=
             HOTRG_OK)
             return s;
     } else if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, T_out)) != HOTRG_OK) {
@@ -569,10 +580,10 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     if (Ti_in) {
         // T_imp' = [P^T (T_imp above T) P + P^T (T above T_imp) P] / (2 c_k)
         if (blocks) {
-            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Tc, Ti_out)) !=
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Tc, Ti_out, piW, piZ)) !=
                 HOTRG_OK)
                 return s;
-            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Tc, Ti2)) !=
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Tc, Ti2, piW, piZ)) !=
                 HOTRG_OK)
                 return s;
         } else {

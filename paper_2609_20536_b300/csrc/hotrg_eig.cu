@@ -50,7 +50,13 @@ constexpr int BCAP_MAX = 112;  // largest subspace width (Rayleigh-Ritz block in
 constexpr int SUB_THREADS = 512;
 constexpr int SUB_ITERS = 12;
 constexpr int SUB_ITERS_U1 = 6;
-constexpr size_t RR_SMEM_BYTES = 2 * BCAP_MAX * BCAP_MAX * sizeof(double) + (BCAP_MAX / 2) * JAC_PAIR_BYTES + 1024;
+// Rayleigh-Ritz finish: H and W (b x b each), the rotation parameters, and a staging area for
+// row chunks of Q and Y (24 KB: 14 rows at b = 112, 64 at b = 24)
+constexpr size_t RR_STAGE_BYTES = 24 * 1024;
+constexpr size_t RR_SMEM_BYTES =
+    2 * BCAP_MAX * BCAP_MAX * sizeof(double) + (BCAP_MAX / 2) * JAC_PAIR_BYTES + RR_STAGE_BYTES + 1024;
+constexpr size_t PREP_SMEM_BYTES = BCAP_MAX * BCAP_MAX * sizeof(double) + RR_STAGE_BYTES;      // G, staging
+constexpr size_t NEXT_SMEM_BYTES = 2 * BCAP_MAX * BCAP_MAX * sizeof(double) + RR_STAGE_BYTES;  // G, W, staging
 constexpr int GB_ROWS = 32;  // rows of E_q per CTA in the FP64 product
 
 struct EigWs {
@@ -66,8 +72,8 @@ struct EigWs {
     int32_t* cand_sec;   // [n] block of each candidate slot
     // per side
     double* A[2];   // m x m regions: FP64 Jacobi work, or the FP32 copy of E_q
-    double* V[2];   // eigenvectors of the block, m x b (ld b), at sec_aoff
-    double* S1[2];  // FP32 Q of the subspace iteration
+    double* V[2];   // eigenvectors of a Jacobi block (b = m), m x m, at sec_aoff
+    double* S1[2];  // FP32 Q of the subspace iteration, then W (b x b: Ritz vectors Q W)
     double* S2[2];  // FP32 Y, then FP64 Q
     double* S3[2];  // FP64 E_q (packed)
     double* S4[2];  // FP64 Y = E_q Q
@@ -165,19 +171,47 @@ __global__ void __launch_bounds__(SORT_THREADS) sectors_kernel(const int32_t* q_
     __syncthreads();
     bitonic_sort_u64(su, npow2);
     for (int i = threadIdx.x; i < n; i += blockDim.x) w.members[i] = (int32_t)(su[i] & 0xffffffffu);
+    // block heads (a key differing from its predecessor's): each warp takes one contiguous range
+    // of the sorted list, counts its heads by ballots, and writes them at its offset (an exclusive
+    // scan over the warps' counts), so sec_start lists the heads in order
+    __shared__ int wcount[SORT_THREADS / 32], woff[SORT_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = ((n + nw - 1) / nw + 31) / 32 * 32;
+    const int lo = warp * per, hi = min(n, lo + per);
+    auto key_of = [&](int i) { return (int)(su[i] >> 32) - (1 << 30); };
+    int cnt = 0;
+    for (int b0 = lo; b0 < hi; b0 += 32) {
+        const int i = b0 + lane;
+        const bool head = i < hi && (i == 0 || key_of(i) != key_of(i - 1));
+        cnt += __popc(__ballot_sync(0xffffffffu, head));
+    }
+    if (lane == 0) wcount[warp] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ns = 0;
-        int prev_key = 0;
-        for (int i = 0; i < n; ++i) {
-            const int key = (int)(su[i] >> 32) - (1 << 30);
-            if (i == 0 || key != prev_key) {
-                w.sec_start[ns] = i;
-                w.sec_key[ns] = key;
-                ++ns;
-                prev_key = key;
-            }
+        int run = 0;
+        for (int v = 0; v < nw; ++v) {
+            woff[v] = run;
+            run += wcount[v];
         }
+        *w.nsec = run;
+    }
+    __syncthreads();
+    int pos = woff[warp];
+    for (int b0 = lo; b0 < hi; b0 += 32) {
+        const int i = b0 + lane;
+        const bool head = i < hi && (i == 0 || key_of(i) != key_of(i - 1));
+        const unsigned m = __ballot_sync(0xffffffffu, head);
+        if (head) {
+            const int slot = pos + __popc(m & ((1u << lane) - 1u));
+            w.sec_start[slot] = i;
+            w.sec_key[slot] = key_of(i);
+        }
+        pos += __popc(m);
+    }
+    __syncthreads();
+    const int ns = *w.nsec;
+    // per-block sizes and offsets (a few dozen blocks: one thread)
+    if (threadIdx.x == 0) {
         w.sec_start[ns] = n;
         int64_t off = 0;
         int cs = 0;
@@ -187,17 +221,19 @@ __global__ void __launch_bounds__(SORT_THREADS) sectors_kernel(const int32_t* q_
             w.sec_aoff[s] = off;
             w.sec_b[s] = b;
             w.sec_cstart[s] = cs;
-            for (int j = 0; j < b; ++j) w.cand_sec[cs + j] = s;
             off += (int64_t)m * m;
             cs += b;
         }
         w.sec_cstart[ns] = cs;
-        *w.nsec = ns;
         *w.ncand = cs;
         w.sweeps[0] = 0;
         w.sweeps[1] = 0;
         *w.status = HOTRG_OK;
     }
+    __syncthreads();
+    // candidate slot -> block, a warp per block
+    for (int s = warp; s < ns; s += nw)
+        for (int j = w.sec_cstart[s] + lane; j < w.sec_cstart[s + 1]; j += 32) w.cand_sec[j] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -859,16 +895,105 @@ __global__ void __launch_bounds__(SUB_THREADS) subspace_fast_kernel(const double
     }
 }
 
-// FP64 basis: Q64 = CGS2(double(Q32)), in S2.
+// Entry k of the upper triangle of a b x b matrix, rows in order: row i starts at
+// S(i) = i b - i (i - 1) / 2; i from the quadratic's root in FP32 (exact integers below 2^24),
+// then corrected by whole rows.
+__device__ __forceinline__ void tri_entry(int k, int b, int& i, int& j) {
+    const float c = (float)(2 * b + 1);
+    i = (int)((c - sqrtf(c * c - 8.0f * (float)k)) * 0.5f);
+    i = max(0, min(i, b - 1));
+    while (i + 1 < b && (i + 1) * b - (i + 1) * i / 2 <= k) ++i;
+    while (i > 0 && i * b - i * (i - 1) / 2 > k) --i;
+    j = i + (k - (i * b - i * (i - 1) / 2));
+}
+
+// Upper triangle of H = X^T Y (X, Y: m x b row-major in global memory; i <= j), accumulated in
+// H[i * b + j] in row order.  Rows are staged R at a time (R b contiguous doubles of each
+// operand, so every global read is coalesced); each thread owns a fixed set of entries, walked
+// in a dense enumeration of the triangle.  Ends with a block barrier.
+__device__ void gram_upper(const double* X, const double* Y, int m, int b, double* H, double* stage, int R) {
+    const int ntri = b * (b + 1) / 2;
+    for (int k = threadIdx.x; k < ntri; k += blockDim.x) {
+        int i, j;
+        tri_entry(k, b, i, j);
+        H[i * b + j] = 0.0;
+    }
+    double* xs = stage;
+    double* ys = stage + R * b;
+    for (int t0 = 0; t0 < m; t0 += R) {
+        const int r = min(R, m - t0);
+        __syncthreads();  // the previous chunk has been consumed
+        for (int e = threadIdx.x; e < r * b; e += blockDim.x) {
+            xs[e] = X[(int64_t)t0 * b + e];
+            ys[e] = Y[(int64_t)t0 * b + e];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < ntri; k += blockDim.x) {
+            int i, j;
+            tri_entry(k, b, i, j);
+            double a = H[i * b + j];
+            for (int u = 0; u < r; ++u) a = fma(xs[u * b + i], ys[u * b + j], a);
+            H[i * b + j] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// One warp: in-place Cholesky G = R^T R of a b x b Gram matrix of unit-norm columns (R upper,
+// in G's upper triangle).  A pivot at or below 1e-8 marks its column dependent or zeroed: it is
+// dropped (live[j] = 0, row j of R set to e_j).  rinv[j] = 1 / R_jj, so that the solve below
+// multiplies (an FP64 divide is a long instruction sequence on this part).
+__device__ void chol_upper_warp(double* G, int b, int* live, double* rinv) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < b; ++j) {
+        const double d = G[j * b + j];
+        __syncwarp();
+        const bool ok = d > 1e-8;
+        const double rjj = ok ? sqrt(d) : 1.0;
+        const double ri = 1.0 / rjj;
+        if (lane == 0) {
+            live[j] = ok ? 1 : 0;
+            rinv[j] = ri;
+        }
+        for (int c = j + lane; c < b; c += 32) G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] * ri) : (c == j ? 1.0 : 0.0);
+        __syncwarp();
+        // trailing update: G[r][c] -= R[j][r] R[j][c] for j < r <= c
+        for (int idx = lane; idx < b * b; idx += 32) {
+            const int r = idx / b, c = idx % b;
+            if (r > j && c >= r) G[r * b + c] -= G[j * b + r] * G[j * b + c];
+        }
+        __syncwarp();
+    }
+}
+
+// Q <- Q R^-1 row by row (forward substitution x R = q, in place: q[i], i < j, already holds
+// x_i); dropped columns become zero.  Ends with a block barrier.
+__device__ void chol_solve_rows(double* Q, int m, int b, const double* G, const int* live, const double* rinv) {
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        double* q = Q + (int64_t)t * b;
+        for (int j = 0; j < b; ++j) {
+            if (!live[j]) {
+                q[j] = 0.0;
+                continue;
+            }
+            double a = q[j];
+            for (int i = 0; i < j; ++i) a = fma(-q[i], G[i * b + j], a);
+            q[j] = a * rinv[j];
+        }
+    }
+    __syncthreads();
+}
+
 // FP64 basis from the FP32 one: Q64 = double(Q32) R^-1 with R the Cholesky
 // factor of G = Q64^T Q64 (one Cholesky QR).  The FP32 basis is orthonormal
 // to ~1e-7, so G is within ~1e-7 of the identity and one pass leaves Q64
 // orthonormal to rounding.  A column whose pivot falls below 1e-8 of its
 // diagonal (a column the FP32 stage zeroed, or a dependent one) is set to
 // zero and dropped from the factorisation.  Result in S2, m x b row-major.
-__global__ void __launch_bounds__(SUB_THREADS) rr_prep_kernel(EigWs w) {
-    extern __shared__ double G[];  // bcap x bcap, sized at launch
+__global__ void __launch_bounds__(SUB_THREADS) rr_prep_kernel(EigWs w, int smem_doubles) {
+    extern __shared__ double G[];  // b x b, then the row-chunk staging area (smem_doubles in all)
     __shared__ int live[BCAP_MAX];
+    __shared__ double rinv[BCAP_MAX];
     const int side = blockIdx.y;
     const int nsec = *w.nsec;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -882,52 +1007,13 @@ __global__ void __launch_bounds__(SUB_THREADS) rr_prep_kernel(EigWs w) {
         for (int t = warp; t < m; t += nw)
             for (int j = lane; j < b; j += 32) Q[(int64_t)t * b + j] = (double)Q32[(int64_t)j * m + t];
         __syncthreads();
-        // G = Q^T Q (upper triangle, one dot product per warp task)
-        for (int task = warp; task < b * b; task += nw) {
-            const int i = task / b, j = task % b;
-            if (i > j) continue;
-            double a = 0.0;
-            for (int t = lane; t < m; t += 32) a = fma(Q[(int64_t)t * b + i], Q[(int64_t)t * b + j], a);
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) {
-                G[i * b + j] = a;
-                G[j * b + i] = a;
-            }
-        }
+        // G = Q^T Q, upper triangle (all the Cholesky reads), from row chunks staged in shared
+        // memory, FP64 FMAs only (widening the FP32 basis inside this loop made the kernel 30%
+        // slower: each conversion is one more FP64-pipe instruction)
+        gram_upper(Q, Q, m, b, G, G + b * b, min(128, (smem_doubles - b * b) / (2 * b)));
+        if (warp == 0) chol_upper_warp(G, b, live, rinv);
         __syncthreads();
-        // in-place Cholesky G = R^T R (R upper, stored in G's upper triangle), one warp
-        if (warp == 0) {
-            for (int j = 0; j < b; ++j) {
-                const double d = G[j * b + j];
-                __syncwarp();
-                const bool ok = d > 1e-8;  // unit-norm columns: d ~ 1 unless dependent or zeroed
-                if (lane == 0) live[j] = ok ? 1 : 0;
-                const double rjj = ok ? sqrt(d) : 1.0;
-                for (int c = j + lane; c < b; c += 32) G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] / rjj) : (c == j ? 1.0 : 0.0);
-                __syncwarp();
-                // trailing update: G[r][c] -= R[j][r] R[j][c] for j < r <= c
-                for (int idx = lane; idx < b * b; idx += 32) {
-                    const int r = idx / b, c = idx % b;
-                    if (r > j && c >= r) G[r * b + c] -= G[j * b + r] * G[j * b + c];
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        // Q <- Q R^-1 row by row (forward substitution x R = q); dropped columns become zero
-        for (int t = tid; t < m; t += blockDim.x) {
-            double* q = Q + (int64_t)t * b;  // in place: q[i], i < j, already holds x_i
-            for (int j = 0; j < b; ++j) {
-                if (!live[j]) {
-                    q[j] = 0.0;
-                    continue;
-                }
-                double a = q[j];
-                for (int i = 0; i < j; ++i) a = fma(-q[i], G[i * b + j], a);
-                q[j] = a / G[j * b + j];
-            }
-        }
-        __syncthreads();
+        chol_solve_rows(Q, m, b, G, live, rinv);
     }
 }
 
@@ -983,7 +1069,9 @@ __global__ void __launch_bounds__(256) rr_product_kernel(EigWs w) {
     }
 }
 
-// H = Q^T Y, Jacobi on H, V = Q W; eigenvalues and the unlisted weight.
+// H = Q^T Y (Y = E_q Q; exactly symmetric: the upper triangle is mirrored), Jacobi on H, W to
+// S1; eigenvalues and the unlisted weight.  The Ritz vectors Q W are formed by the projector,
+// for the kept columns only.
 __global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, double tol, EigWs w) {
     extern __shared__ double sm[];
     __shared__ double red[40];
@@ -999,46 +1087,25 @@ __global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, 
         const double* Y = w.S4[side] + aoff;
         const double* E = w.S3[side] + aoff;
         double* H = sm;
-        double* W = sm + BCAP_MAX * BCAP_MAX;
-        double* rc = sm + 2 * BCAP_MAX * BCAP_MAX;
+        double* W = sm + b * b;
+        double* rc = sm + 2 * b * b;
         double* rs = rc + BCAP_MAX / 2;
         int* rp = (int*)(rs + BCAP_MAX / 2);
         int* rq = rp + BCAP_MAX / 2;
-        // H = Q^T Y, symmetrised: one warp per entry, lanes striding the m rows (a thread per entry
-        // walking all m rows made this product latency-bound)
-        {
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-            for (int idx = warp; idx < b * b; idx += nw) {
-                const int i = idx / b, j = idx % b;
-                double a = 0.0;
-                for (int t = lane; t < m; t += 32) a = fma(Q[(int64_t)t * b + i], Y[(int64_t)t * b + j], a);
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (lane == 0) H[idx] = a;
-            }
-        }
-        __syncthreads();
+        double* stage = (double*)(rq + BCAP_MAX / 2);
+        const int avail = (int)(RR_SMEM_BYTES / sizeof(double)) - (int)(stage - sm);
+        const int R = min(128, avail / (2 * b));
+        gram_upper(Q, Y, m, b, H, stage, R);
         for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
             const int i = idx / b, j = idx % b;
-            if (i < j) {
-                const double s = 0.5 * (H[i * b + j] + H[j * b + i]);
-                H[i * b + j] = s;
-                H[j * b + i] = s;
-            }
+            if (i > j) H[idx] = H[j * b + i];
         }
         __syncthreads();
         const int sw = jacobi_block(H, W, b, max_sweeps, tol, rc, rs, rp, rq, red, &s_rot);
-        // W (b x b) is kept for a further FP64 iteration (rr_next_kernel): the FP32 basis that
-        // S1 held has been consumed by rr_prep_kernel
+        // W (b x b) to S1, for the projector (Ritz vectors) and for a further FP64 iteration
+        // (rr_next_kernel): the FP32 basis that S1 held has been consumed by rr_prep_kernel
         double* Wg = w.S1[side] + aoff;
         for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) Wg[idx] = W[idx];
-        // Ritz vectors V = Q W (m x b)
-        double* V = w.V[side] + aoff;
-        for (int64_t idx = threadIdx.x; idx < (int64_t)m * b; idx += blockDim.x) {
-            const int t = (int)(idx / b), j = (int)(idx % b);
-            double a = 0.0;
-            for (int i = 0; i < b; ++i) a = fma(Q[(int64_t)t * b + i], W[i * b + j], a);
-            V[idx] = a;
-        }
         const int cs = w.sec_cstart[sct];
         for (int j = threadIdx.x; j < b; j += blockDim.x) w.lam[side][cs + j] = H[j * b + j];
         // unlisted weight: Tr(E_q) - sum of the listed eigenvalues
@@ -1065,9 +1132,10 @@ __global__ void __launch_bounds__(JAC_THREADS) rr_finish_kernel(int max_sweeps, 
 // 1e-8 of their unit norm) orthonormalises them to rounding.  Each such
 // iteration shrinks the error of the j-th Ritz vector by lambda_{b+1} /
 // lambda_j.  Result in S2 (m x b row-major), ready for rr_product_kernel.
-__global__ void __launch_bounds__(SUB_THREADS) rr_next_kernel(EigWs w) {
-    extern __shared__ double G[];  // bcap x bcap (the Gram matrix), then bcap x bcap (W)
+__global__ void __launch_bounds__(SUB_THREADS) rr_next_kernel(EigWs w, int smem_doubles) {
+    extern __shared__ double G[];  // b x b (the Gram matrix), b x b (W), then row-chunk staging
     __shared__ int live[BCAP_MAX];
+    __shared__ double rinv[BCAP_MAX];
     __shared__ double cn[BCAP_MAX];
     const int side = blockIdx.y;
     const int nsec = *w.nsec;
@@ -1099,48 +1167,10 @@ __global__ void __launch_bounds__(SUB_THREADS) rr_next_kernel(EigWs w) {
         __syncthreads();
         for (int64_t idx = tid; idx < (int64_t)m * b; idx += blockDim.x) Z[idx] *= cn[(int)(idx % b)];
         __syncthreads();
-        for (int task = warp; task < b * b; task += nw) {
-            const int i = task / b, j = task % b;
-            if (i > j) continue;
-            double a = 0.0;
-            for (int t = lane; t < m; t += 32) a = fma(Z[(int64_t)t * b + i], Z[(int64_t)t * b + j], a);
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) {
-                G[i * b + j] = a;
-                G[j * b + i] = a;
-            }
-        }
+        gram_upper(Z, Z, m, b, G, G + 2 * b * b, min(128, (smem_doubles - 2 * b * b) / (2 * b)));
+        if (warp == 0) chol_upper_warp(G, b, live, rinv);
         __syncthreads();
-        if (warp == 0) {
-            for (int j = 0; j < b; ++j) {
-                const double d = G[j * b + j];
-                __syncwarp();
-                const bool ok = d > 1e-8;
-                if (lane == 0) live[j] = ok ? 1 : 0;
-                const double rjj = ok ? sqrt(d) : 1.0;
-                for (int c = j + lane; c < b; c += 32) G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] / rjj) : (c == j ? 1.0 : 0.0);
-                __syncwarp();
-                for (int idx = lane; idx < b * b; idx += 32) {
-                    const int r = idx / b, c = idx % b;
-                    if (r > j && c >= r) G[r * b + c] -= G[j * b + r] * G[j * b + c];
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        for (int t = tid; t < m; t += blockDim.x) {
-            double* q = Z + (int64_t)t * b;
-            for (int j = 0; j < b; ++j) {
-                if (!live[j]) {
-                    q[j] = 0.0;
-                    continue;
-                }
-                double a = q[j];
-                for (int i = 0; i < j; ++i) a = fma(-q[i], G[i * b + j], a);
-                q[j] = a / G[j * b + j];
-            }
-        }
-        __syncthreads();
+        chol_solve_rows(Z, m, b, G, live, rinv);
     }
 }
 
@@ -1306,8 +1336,20 @@ __global__ void projector_kernel(int dprime, int policy, double side_rtol, EigWs
     const int m = w.sec_start[sct + 1] - start;
     const int b = w.sec_b[sct];
     const int pos = slot - w.sec_cstart[sct];
-    const double* V = w.V[side] + w.sec_aoff[sct];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) P[(int64_t)w.members[start + i] * dprime + j] = V[(int64_t)i * b + pos];
+    const int64_t aoff = w.sec_aoff[sct];
+    if (b == m) {  // a Jacobi block: its eigenvectors are stored
+        const double* V = w.V[side] + aoff;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) P[(int64_t)w.members[start + i] * dprime + j] = V[(int64_t)i * b + pos];
+    } else {  // a subspace block: Ritz vector Q W[:, pos] (Q in S2, m x b; W in S1, b x b)
+        const double* Q = w.S2[side] + aoff;
+        const double* Wc = w.S1[side] + aoff + pos;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double* q = Q + (int64_t)i * b;
+            double a = 0.0;
+            for (int c = 0; c < b; ++c) a = fma(q[c], Wc[(int64_t)c * b], a);
+            P[(int64_t)w.members[start + i] * dprime + j] = a;
+        }
+    }
     if (threadIdx.x == 0) q_out[j] = w.sec_key[sct];
     if (j == 0 && threadIdx.x == 0 && info) {
         info->eps_left = eL;
@@ -1336,9 +1378,9 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(subspace_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  SUBF_SMEM));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 BCAP_MAX * BCAP_MAX * (int)sizeof(double)));
+                                                 (int)PREP_SMEM_BYTES));
         HOTRG_CUDA_TRY(ctx, cudaFuncSetAttribute(rr_next_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 2 * BCAP_MAX * BCAP_MAX * (int)sizeof(double)));
+                                                 (int)NEXT_SMEM_BYTES));
     }
     EigWs w = carve(ws, n);
     // listed width of large blocks in the split forms
@@ -1400,7 +1442,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         prof_end(ctx, hp1, PROF_EIG_PART0 + 1, 0.0);
         HOTRG_LAUNCH_CHECK(ctx, "subspace_fp32_kernel");
         const int hp2 = prof_begin(ctx);
-        rr_prep_kernel<<<dim3(sgrid, sides), SUB_THREADS, (size_t)bcap * bcap * sizeof(double), st>>>(w);
+        const size_t prep_smem = (size_t)bcap * bcap * sizeof(double) + RR_STAGE_BYTES;
+        rr_prep_kernel<<<dim3(sgrid, sides), SUB_THREADS, prep_smem, st>>>(w, (int)(prep_smem / sizeof(double)));
         HOTRG_LAUNCH_CHECK(ctx, "rr_prep_kernel");
         const int tiles = (n + GB_ROWS - 1) / GB_ROWS;
         rr_product_kernel<<<dim3(tiles < 64 ? tiles : 64, sgrid < 32 ? sgrid : 32, sides), 256, 0, st>>>(w);
@@ -1409,7 +1452,8 @@ hotrg_status eig_truncate(hotrg_ctx* ctx, const EigPlan& plan, const double* EL,
         HOTRG_LAUNCH_CHECK(ctx, "rr_finish_kernel");
         // further FP64 subspace iterations, each followed by its Rayleigh-Ritz step
         for (int r = 0; r < plan.fp64_iters; ++r) {
-            rr_next_kernel<<<dim3(sgrid, sides), SUB_THREADS, (size_t)2 * bcap * bcap * sizeof(double), st>>>(w);
+            const size_t next_smem = (size_t)2 * bcap * bcap * sizeof(double) + RR_STAGE_BYTES;
+            rr_next_kernel<<<dim3(sgrid, sides), SUB_THREADS, next_smem, st>>>(w, (int)(next_smem / sizeof(double)));
             rr_product_kernel<<<dim3(tiles < 64 ? tiles : 64, sgrid < 32 ? sgrid : 32, sides), 256, 0, st>>>(w);
             rr_finish_kernel<<<dim3(sgrid, sides), JAC_THREADS, RR_SMEM_BYTES, st>>>(plan.max_sweeps, plan.tol, w);
             HOTRG_COUNT(3);

@@ -13,7 +13,7 @@
 // are staged in shared memory; the operand elements are gathered through them
 // (A(m, k) = A[offM0[m] + offK0[k]], B(n, k) = B[offN0[n] + offK1[k]]) and
 // each thread accumulates a 4 x 4 block of outputs, written to
-// C[offM1[m] + offN1[n]].
+// C[offM1[m] + offN1[n]] (+ pi_out[offM2[m] + offN2[n]] for an output in a pair layout).
 #include "internal.cuh"
 
 namespace hotrg {
@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(DG_THREADS) dgemm_grouped_kernel(const double*
     __shared__ double Bs[DG_K][DG_T + 1];
     __shared__ int64_t rA[DG_T], rB[DG_T], rC[DG_T], cC[DG_T];
     __shared__ int64_t kA[DG_K], kB[DG_K];
+    __shared__ int32_t rP[DG_T], cP[DG_T];
+    const int32_t* __restrict__ pi = pl.pi_out;
     const int G = pl.hdr->G;
     const int total = pl.hdr->total_tiles * 4;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -56,10 +58,12 @@ __global__ void __launch_bounds__(DG_THREADS) dgemm_grouped_kernel(const double*
             const int m = m0 + tid;
             rA[tid] = m < gr.M ? pl.offM0[gr.mbase + m] : -1;
             rC[tid] = m < gr.M ? pl.offM1[gr.mbase + m] : -1;
+            rP[tid] = (m < gr.M && pi) ? pl.offM2[gr.mbase + m] : 0;
         } else if (tid < 2 * DG_T) {
             const int n = n0 + tid - DG_T;
             rB[tid - DG_T] = n < gr.N ? pl.offN0[gr.nbase + n] : -1;
             cC[tid - DG_T] = n < gr.N ? pl.offN1[gr.nbase + n] : -1;
+            cP[tid - DG_T] = (n < gr.N && pi) ? pl.offN2[gr.nbase + n] : 0;
         }
         double acc[4][4];
 #pragma unroll
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(DG_THREADS) dgemm_grouped_kernel(const double*
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t co = cC[tx + 16 * j];
-                if (co >= 0) C[ro + co] = acc[i][j];
+                if (co >= 0) C[ro + co + (pi ? (int64_t)pi[rP[ty + 16 * i] + cP[tx + 16 * j]] : 0)] = acc[i][j];
             }
         }
     }

@@ -81,16 +81,75 @@ __device__ __forceinline__ uint64_t fixed_f64(double v, int sh) {
     return (mant + (1ull << (r - 1))) >> r;
 }
 
-__device__ __forceinline__ uint64_t fixed_f32(float v, int sh) {
-    const uint32_t b = __float_as_uint(v);
+// round(|v| 2^sh) with v's sign, from an FP32 bit pattern (|v| 2^sh < 2^39; 0 for zero or
+// subnormal v).
+__device__ __forceinline__ int64_t fixed_half(uint32_t b, int sh) {
     const int ex = (int)((b >> 23) & 0xff);
     if (ex == 0) return 0;
-    const uint64_t mant = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+    const uint32_t mant = (b & 0x7fffffu) | 0x800000u;
     const int s = ex - 150 + sh;
-    if (s >= 0) return s >= 39 ? 0 : (mant << s);
-    const int r = -s;
-    if (r >= 63) return 0;
-    return (mant + (1ull << (r - 1))) >> r;
+    int64_t a;
+    if (s >= 0) {
+        a = s >= 39 ? 0 : ((int64_t)mant << s);
+    } else {
+        const int r = -s;
+        a = r > 24 ? 0 : (int64_t)((mant + (1u << (r - 1))) >> r);  // below 1/2 when r > 24
+    }
+    return (b >> 31) ? -a : a;
+}
+
+// Fixed-point value F = round(v 2^sh) of one element from its 8-byte pattern: an FP64 value,
+// or an exact FP32 pair hi + lo (hi in the low word, |lo| <= ulp(hi) / 2).  For a pair the two
+// parts are rounded on their own: |hi| 2^sh is an integer whenever |hi| >= 2^(23 - sh), which
+// with five slices (sh = 39 - e for a row whose largest element lies below 2^e) covers every
+// element within 2^-15 of the largest, so F is then exact; for the smaller ones the second
+// rounding adds at most half a unit, the size of the largest element's own rounding error.
+template <int FMT>
+__device__ __forceinline__ int64_t fixed_elem(uint64_t bits, int sh) {
+    if (FMT == FMT_F64) {
+        const int64_t a = (int64_t)fixed_f64(__longlong_as_double((long long)bits), sh);
+        return (bits >> 63) ? -a : a;  // the sign from the bit pattern (no FP64 compare)
+    } else {
+        return fixed_half((uint32_t)(bits & 0xffffffffu), sh) + fixed_half((uint32_t)(bits >> 32), sh);
+    }
+}
+
+// The NS balanced base-256 digits of F (|F| <= 2^(B1 + 8 (NS - 1))): c_0 = round(F / 2^(8 (NS - 1))),
+// each later digit the rounded remainder (round half up), the last the exact remainder, so
+// |c_p| <= 128.  After c_0 the remainder fits 32 bits.  bits[p] = the BF16 pattern of
+// c_p 2^(-8p): c_p has at most 8 significant bits, so its FP32 value truncates to BF16 exactly.
+__device__ __forceinline__ void slice_digits(int64_t F, int NS, uint32_t* bits) {
+    const int sh0 = 8 * (NS - 1);
+    const int64_t c0 = (F >> sh0) + ((F >> (sh0 - 1)) & 1);
+    int32_t r = (int32_t)(F - (c0 << sh0));
+    bits[0] = __float_as_uint((float)c0) >> 16;
+    float scale = 1.0f;
+#pragma unroll
+    for (int p = 1; p < 5; ++p) {
+        if (p < NS) {
+            const int sh = 8 * (NS - 1 - p);
+            int32_t c;
+            if (sh == 0) {
+                c = r;
+            } else {
+                c = (r >> sh) + ((r >> (sh - 1)) & 1);
+                r = (int32_t)((uint32_t)r - ((uint32_t)c << sh));  // exact: the result fits
+            }
+            scale *= 1.0f / 256.0f;
+            bits[p] = __float_as_uint((float)c * scale) >> 16;
+        }
+    }
+}
+
+// Slices of two consecutive elements (o points at the first; even offset) as packed BF16 pairs.
+__device__ __forceinline__ void store_slices2(__nv_bfloat16* o, int64_t slice_stride, int NS, int64_t F0,
+                                              int64_t F1) {
+    uint32_t b0[5], b1[5];
+    slice_digits(F0, NS, b0);
+    slice_digits(F1, NS, b1);
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+        if (p < NS) *(uint32_t*)(o + p * slice_stride) = b0[p] | (b1[p] << 16);
 }
 
 template <int FMT>
@@ -132,34 +191,14 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const void* __restrict_
     if (lane == 0) exps[row] = e;
     const int T = SLICE_B1 + 8 * (NS - 1);
     __nv_bfloat16* o0 = out + row * Kp;
-    for (int k = lane; k < Kp; k += 32) {
-        int64_t F = 0;
-        if (k < K && emax > -2000) {
-            double d = 0.0;
-            float hi = 0.f, lo = 0.f;
-            load_elem<FMT>(X, base + k, d, hi, lo);
-            if (FMT == FMT_F64) {
-                const int64_t a = (int64_t)fixed_f64(d, T - e);
-                F = d < 0.0 ? -a : a;
-            } else {
-                const int G = 16;  // guard bits for the exact integer sum hi + lo
-                const int64_t fh = (int64_t)fixed_f32(hi, T - e + G) * (hi < 0.f ? -1 : 1);
-                const int64_t fl = (int64_t)fixed_f32(lo, T - e + G) * (lo < 0.f ? -1 : 1);
-                F = (fh + fl + (1ll << (G - 1))) >> G;
-            }
+    const uint64_t* Xb = (const uint64_t*)X;
+    for (int k = 2 * lane; k < Kp; k += 64) {  // two elements per lane (Kp is even)
+        int64_t F0 = 0, F1 = 0;
+        if (emax > -2000) {
+            if (k < K) F0 = fixed_elem<FMT>(Xb[base + k], T - e);
+            if (k + 1 < K) F1 = fixed_elem<FMT>(Xb[base + k + 1], T - e);
         }
-        int64_t r = F;
-        for (int p = 0; p < NS; ++p) {
-            const int sh = 8 * (NS - 1 - p);  // = T - B1 - 8p
-            int64_t c;
-            if (sh == 0) {
-                c = r;
-            } else {
-                c = (r + (1ll << (sh - 1))) >> sh;  // round half up (arithmetic shift)
-                r -= c << sh;
-            }
-            o0[p * slice_stride + k] = __float2bfloat16_rn(ldexpf((float)c, -8 * p));
-        }
+        store_slices2(o0 + k, slice_stride, NS, F0, F1);
     }
 }
 
@@ -209,39 +248,17 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_gather_kernel(const v
     if (lane == 0) exps[row] = e;
     const int T = SLICE_B1 + 8 * (NS - 1);
     __nv_bfloat16* o0 = out + row * Kp;
-    for (int k = lane; k < Kp; k += 32) {
-        int64_t F = 0;
-        if (k < K && emax > -2000) {
-            uint64_t bits;
-            if (cached)
-                bits = srow[k];
-            else
-                bits = ((const uint64_t*)X)[rbase + (int64_t)(k / g.kd) * g.ks0 + (int64_t)(k % g.kd) * g.ks1];
-            if (FMT == FMT_F64) {
-                const double d = __longlong_as_double((long long)bits);
-                const int64_t a = (int64_t)fixed_f64(d, T - e);
-                F = d < 0.0 ? -a : a;
-            } else {
-                const float hi = __uint_as_float((uint32_t)(bits & 0xffffffffu));
-                const float lo = __uint_as_float((uint32_t)(bits >> 32));
-                const int G = 16;
-                const int64_t fh = (int64_t)fixed_f32(hi, T - e + G) * (hi < 0.f ? -1 : 1);
-                const int64_t fl = (int64_t)fixed_f32(lo, T - e + G) * (lo < 0.f ? -1 : 1);
-                F = (fh + fl + (1ll << (G - 1))) >> G;
-            }
+    const uint64_t* Xb = (const uint64_t*)X;
+    auto elem = [&](int k) -> uint64_t {
+        return cached ? srow[k] : Xb[rbase + (int64_t)(k / g.kd) * g.ks0 + (int64_t)(k % g.kd) * g.ks1];
+    };
+    for (int k = 2 * lane; k < Kp; k += 64) {  // two elements per lane (Kp is even)
+        int64_t F0 = 0, F1 = 0;
+        if (emax > -2000) {
+            if (k < K) F0 = fixed_elem<FMT>(elem(k), T - e);
+            if (k + 1 < K) F1 = fixed_elem<FMT>(elem(k + 1), T - e);
         }
-        int64_t r = F;
-        for (int p = 0; p < NS; ++p) {
-            const int sh = 8 * (NS - 1 - p);
-            int64_t c;
-            if (sh == 0) {
-                c = r;
-            } else {
-                c = (r + (1ll << (sh - 1))) >> sh;
-                r -= c << sh;
-            }
-            o0[p * slice_stride + k] = __float2bfloat16_rn(ldexpf((float)c, -8 * p));
-        }
+        store_slices2(o0 + k, slice_stride, NS, F0, F1);
     }
 }
 
@@ -726,19 +743,6 @@ hotrg_status umma_gemm_fmt(hotrg_ctx* ctx, int prec, int M, int N, int K, const 
     return launch_umma<3>(ctx, As, Bs, M, N, Kp, a);
 }
 
-static GatherMap plain_map(int64_t ld) {
-    GatherMap g;
-    g.rd1 = 1;
-    g.rd2 = 1;
-    g.rs0 = ld;
-    g.rs1 = 0;
-    g.rs2 = 0;
-    g.kd = 1 << 30;
-    g.ks0 = 0;
-    g.ks1 = 1;
-    return g;
-}
-
 // C = A B^T with A and B read through gather maps (both FP64 or FP32-pair).
 hotrg_status umma_gemm_gather(hotrg_ctx* ctx, int prec, int M, int N, int K, const void* A, const GatherMap& am,
                               int afmt, const void* B, const GatherMap& bm, int bfmt, void* C, int cfmt, int64_t ldc,
@@ -825,7 +829,8 @@ hotrg_status umma_contract(hotrg_ctx* ctx, int prec, int M, int N, int K, const 
 // value) share one slice buffer per operand, laid out group after group with
 // every group padded to 128 rows; row pitch = the K set's size rounded up to
 // 32.  Operand element (m, k) of group g is X[rowoff[mbase_g + m] + koff[kbase_g + k]]
-// and output element (m, n) goes to C[rowC[mbase_g + m] + colC[nbase_g + n]].
+// and output element (m, n) goes to C[rowC[mbase_g + m] + colC[nbase_g + n]], plus
+// pi[rowP[mbase_g + m] + colP[nbase_g + n]] when the output is in a pair layout.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int group_of_row(const BsGroup* gr, int G, int64_t r, bool b_side) {
     int lo = 0, hi = G - 1;
@@ -842,84 +847,80 @@ __device__ __forceinline__ int group_of_row(const BsGroup* gr, int G, int64_t r,
 // One warp per padded slice row; rows beyond the plan's padded total leave at once.
 // X holds FP64 values (FMT_F64) or exact FP32 pairs hi + lo (FMT_F32PAIR).  Rows
 // of up to GROUP_SMEM_K elements are read once (4 KB of shared memory per warp).
+// k_contig: the K offsets of every group are consecutive (koff[kbase + k] =
+// koff[kbase] + k, the case of an operand in a pair layout), so the values are
+// read straight from X without the offset table.
 constexpr int GROUP_SMEM_K = 512;
 template <int FMT>
 __global__ void __launch_bounds__(32 * GATHER_WARPS) slice_grouped_kernel(
     const void* __restrict__ X, const int64_t* __restrict__ rowoff, const int64_t* __restrict__ koff,
-    const BsGroup* __restrict__ groups, const BsHeader* __restrict__ hdr, int b_side, int NS, int Kp,
+    const BsGroup* __restrict__ groups, const BsHeader* __restrict__ hdr, int b_side, int k_contig, int NS, int Kp,
     __nv_bfloat16* __restrict__ out, int64_t slice_stride, int32_t* __restrict__ exps) {
     extern __shared__ uint64_t srow_all[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * GATHER_WARPS + wib;
     const int G = hdr->G;
-    if (G == 0 || r >= (b_side ? hdr->npad_total : hdr->mpad_total)) return;
-    const int g = group_of_row(groups, G, r, b_side != 0);
-    const BsGroup gr = groups[g];
-    const int64_t local = r - (b_side ? gr.npad : gr.mpad);
-    const int rows = b_side ? gr.N : gr.M;
-    const int K = gr.K, Kg = gr.Kp;
-    const int64_t* kof = koff + gr.kbase;
-    __nv_bfloat16* o0 = out + r * Kp;
-    if (local >= rows) {  // padding row of the group's last tile
-        if (lane == 0) exps[r] = 0;
-        for (int k = lane; k < Kg; k += 32)
-            for (int p = 0; p < NS; ++p) o0[p * slice_stride + k] = __float2bfloat16_rn(0.f);
-        return;
-    }
-    const int64_t rbase = rowoff[(b_side ? gr.nbase : gr.mbase) + local];
-    const bool cached = K <= GROUP_SMEM_K;
+    const int64_t rows_total = b_side ? hdr->npad_total : hdr->mpad_total;
     uint64_t* srow = srow_all + (size_t)wib * GROUP_SMEM_K;
-    int emax = -2000;
-    // four elements per lane in flight: offsets first, then the values they point at
-    for (int k0 = lane; k0 < K; k0 += 128) {
-        int64_t o[4];
-        uint64_t v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) o[u] = k0 + 32 * u < K ? kof[k0 + 32 * u] : 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = k0 + 32 * u < K ? ((const uint64_t*)X)[rbase + o[u]] : 0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = k0 + 32 * u;
-            if (k < K) {
-                if (cached) srow[k] = v[u];
-                const int ex = FMT == FMT_F64 ? exp_f64(__longlong_as_double((long long)v[u]))
-                                              : exp_f32(__uint_as_float((uint32_t)(v[u] & 0xffffffffu)));
-                emax = max(emax, ex);
-            }
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    __syncwarp();
-    const int e = emax <= -2000 ? 0 : emax + 1;
-    if (lane == 0) exps[r] = e;
+    const uint64_t* Xb = (const uint64_t*)X;
     const int T = SLICE_B1 + 8 * (NS - 1);
-    for (int k = lane; k < Kg; k += 32) {
-        int64_t F = 0;
-        if (k < K && emax > -2000) {
-            const uint64_t bits = cached ? srow[k] : ((const uint64_t*)X)[rbase + kof[k]];
-            if (FMT == FMT_F64) {
-                const int64_t a = (int64_t)fixed_f64(__longlong_as_double((long long)bits), T - e);
-                F = (bits >> 63) ? -a : a;  // the sign from the bit pattern (no FP64 compare)
+    const int64_t r = (int64_t)blockIdx.x * GATHER_WARPS + wib;
+    if (G == 0 || r >= rows_total) return;
+    {
+        const int g = group_of_row(groups, G, r, b_side != 0);
+        const BsGroup gr = groups[g];
+        const int64_t local = r - (b_side ? gr.npad : gr.mpad);
+        const int rows = b_side ? gr.N : gr.M;
+        const int K = gr.K, Kg = gr.Kp;
+        const int64_t* kof = koff + gr.kbase;
+        __nv_bfloat16* o0 = out + r * Kp;
+        if (local >= rows) {  // padding row of the group's last tile
+            if (lane == 0) exps[r] = 0;
+            for (int k = lane; k < Kg; k += 32)
+                for (int p = 0; p < NS; ++p) o0[p * slice_stride + k] = __float2bfloat16_rn(0.f);
+            return;
+        }
+        // the row's base and, for consecutive K offsets, the first of them (independent loads)
+        const int64_t rbase = rowoff[(b_side ? gr.nbase : gr.mbase) + local] + ((k_contig && K > 0) ? kof[0] : 0);
+        const bool cached = K <= GROUP_SMEM_K;
+        int emax = -2000;
+        // four elements per lane in flight
+        for (int k0 = lane; k0 < K; k0 += 128) {
+            uint64_t v[4];
+            if (k_contig) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = k0 + 32 * u < K ? Xb[rbase + k0 + 32 * u] : 0;
             } else {
-                const uint32_t hb = (uint32_t)(bits & 0xffffffffu), lb = (uint32_t)(bits >> 32);
-                const int G = 16;  // guard bits for the exact integer sum hi + lo
-                const int64_t fh = (int64_t)fixed_f32(__uint_as_float(hb), T - e + G) * ((hb >> 31) ? -1 : 1);
-                const int64_t fl = (int64_t)fixed_f32(__uint_as_float(lb), T - e + G) * ((lb >> 31) ? -1 : 1);
-                F = (fh + fl + (1ll << (G - 1))) >> G;
+                int64_t o[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) o[u] = k0 + 32 * u < K ? kof[k0 + 32 * u] : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = k0 + 32 * u < K ? Xb[rbase + o[u]] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + 32 * u;
+                if (k < K) {
+                    if (cached) srow[k] = v[u];
+                    const int ex = FMT == FMT_F64 ? exp_f64(__longlong_as_double((long long)v[u]))
+                                                  : exp_f32(__uint_as_float((uint32_t)(v[u] & 0xffffffffu)));
+                    emax = max(emax, ex);
+                }
             }
         }
-        int64_t rem = F;
-        for (int p = 0; p < NS; ++p) {
-            const int sh = 8 * (NS - 1 - p);
-            int64_t c;
-            if (sh == 0) {
-                c = rem;
-            } else {
-                c = (rem + (1ll << (sh - 1))) >> sh;
-                rem -= c << sh;
+        for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+        __syncwarp();
+        const int e = emax <= -2000 ? 0 : emax + 1;
+        if (lane == 0) exps[r] = e;
+        auto elem = [&](int k) -> uint64_t {
+            return cached ? srow[k] : Xb[rbase + (k_contig ? (int64_t)k : kof[k])];
+        };
+        for (int k = 2 * lane; k < Kg; k += 64) {  // two elements per lane (Kg is even)
+            int64_t F0 = 0, F1 = 0;
+            if (emax > -2000) {
+                if (k < K) F0 = fixed_elem<FMT>(elem(k), T - e);
+                if (k + 1 < K) F1 = fixed_elem<FMT>(elem(k + 1), T - e);
             }
-            o0[p * slice_stride + k] = __float2bfloat16_rn(ldexpf((float)c, -8 * p));
+            store_slices2(o0 + k, slice_stride, NS, F0, F1);
         }
     }
 }
@@ -931,6 +932,9 @@ struct GroupArgs {
     const int32_t* eB;
     const int64_t* rowC;
     const int64_t* colC;
+    const int32_t* pi;  // null, or the output's pair table with its row / column parts
+    const int32_t* rowP;
+    const int32_t* colP;
     void* C;
     int32_t* status;
 };
@@ -1009,7 +1013,10 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
     const int G = args.hdr->G;
     const int total = args.hdr->total_tiles;
     __shared__ int s_abort;
+    // the group table, read by every tile's decode (a binary search) and by its epilogue
+    __shared__ BsGroup sgr[BS_V];
     if (threadIdx.x == 0) s_abort = *(volatile const int32_t*)args.status;
+    for (int i = threadIdx.x; i < G; i += blockDim.x) sgr[i] = args.groups[i];
     __syncthreads();
     if (s_abort != 0 || G == 0 || (int)blockIdx.x >= total) return;
 
@@ -1042,8 +1049,8 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 int g, tm, tn;
-                decode_tile(args.groups, G, t, g, tm, tn);
-                const BsGroup gr = args.groups[g];
+                decode_tile(sgr, G, t, g, tm, tn);
+                const BsGroup& gr = sgr[g];
                 const int nkb = gr.Kp / BK;
                 const int arow = (int)(gr.mpad + (int64_t)tm * BM), brow = (int)(gr.npad + (int64_t)tn * TBN);
                 for (int kb = 0; kb < nkb; ++kb) {
@@ -1075,8 +1082,8 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 int g, tm, tn;
-                decode_tile(args.groups, G, t, g, tm, tn);
-                const int nkb = args.groups[g].Kp / BK;
+                decode_tile(sgr, G, t, g, tm, tn);
+                const int nkb = sgr[g].Kp / BK;
                 for (int kb = 0; kb < nkb; ++kb) {
                     const int s = it % STAGES;
                     const bool chunk_start = (kb % KCB) == 0;
@@ -1141,8 +1148,8 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
         bool alive = true;
         for (int t = blockIdx.x; t < total && alive; t += gridDim.x) {
             int g, tm, tn;
-            decode_tile(args.groups, G, t, g, tm, tn);
-            const BsGroup gr = args.groups[g];
+            decode_tile(sgr, G, t, g, tm, tn);
+            const BsGroup& gr = sgr[g];
             const int nchunks = (gr.Kp / BK + KCB - 1) / KCB;
             float hi[COLS], lo[COLS];
 #pragma unroll
@@ -1185,6 +1192,8 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
             const int my_lrow = tm * BM + row_local;
             const int row_ok = my_lrow < gr.M ? 1 : 0;
             const int64_t my_roff = row_ok ? args.rowC[gr.mbase + my_lrow] : 0;
+            const int32_t* __restrict__ pi = args.pi;
+            const int my_rp = (row_ok && pi) ? args.rowP[gr.mbase + my_lrow] : 0;
             const int my_ea = args.eA[gr.mpad + my_lrow];
             float2* stg = (float2*)(staging + (warp - 2) * (32 * Cfg::STG_LD));
             const int cl = lane & 15;
@@ -1196,6 +1205,7 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                 const int lcol = tn * TBN + colbase + c0 + cl;
                 const bool col_ok = lcol < gr.N;
                 const int64_t coff = col_ok ? args.colC[gr.nbase + lcol] : 0;
+                const int ccp = (col_ok && pi) ? args.colP[gr.nbase + lcol] : 0;
                 const int ceb = col_ok ? args.eB[gr.npad + lcol] : 0;
 #pragma unroll 4
                 for (int r = 0; r < 16; ++r) {
@@ -1203,19 +1213,29 @@ __global__ void __launch_bounds__(THREADS, 1) umma_grouped_kernel(const __grid_c
                     const int64_t roff = __shfl_sync(0xffffffffu, my_roff, row);
                     const int ea = __shfl_sync(0xffffffffu, my_ea, row);
                     const int rok = __shfl_sync(0xffffffffu, row_ok, row);
+                    const int rp = __shfl_sync(0xffffffffu, my_rp, row);
                     if (rok && col_ok) {
+                        const int64_t off = roff + coff + (pi ? (int64_t)__ldg(pi + rp + ccp) : 0);
                         const float2 v = stg[row * Cfg::STG_LD + cl];
                         const int sc = ea + ceb - 2 * SLICE_B1;
                         if (OUT == FMT_F32PAIR) {
-                            // exact pair, scaled in FP32 (no FP64 arithmetic in this epilogue)
-                            ((float2*)args.C)[roff + coff] = make_float2(ldexpf(v.x, sc), ldexpf(v.y, sc));
+                            // exact pair, scaled in FP32 (no FP64 arithmetic in this epilogue): a
+                            // product with the normal float 2^sc rounds exactly as ldexpf does
+                            float2 o;
+                            if (sc >= -126 && sc <= 127) {
+                                const float p2 = __int_as_float((sc + 127) << 23);
+                                o = make_float2(v.x * p2, v.y * p2);
+                            } else {
+                                o = make_float2(ldexpf(v.x, sc), ldexpf(v.y, sc));
+                            }
+                            ((float2*)args.C)[off] = o;
                         } else {
                             // FP64: the power-of-two scale is an add to the exponent field of the
                             // (normal or zero) sum
                             const double d = (double)v.x + (double)v.y;
                             long long b = __double_as_longlong(d);
                             if (b & 0x7ff0000000000000ll) b += (long long)sc << 52;
-                            ((double*)args.C)[roff + coff] = __longlong_as_double(b);
+                            ((double*)args.C)[off] = __longlong_as_double(b);
                         }
                     }
                 }
@@ -1295,19 +1315,20 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
     const int smem = GATHER_WARPS * GROUP_SMEM_K * 8;
     const unsigned gA = (unsigned)((rA + GATHER_WARPS - 1) / GATHER_WARPS);
     const unsigned gB = (unsigned)((rB + GATHER_WARPS - 1) / GATHER_WARPS);
+    const int kc = pl.kA_contig ? 1 : 0;
     const int h_slice = prof_begin(ctx);
     if (afmt == FMT_F64)
         slice_grouped_kernel<FMT_F64><<<gA, 32 * GATHER_WARPS, smem, s>>>(A, pl.offM0, pl.offK0, pl.groups, pl.hdr, 0,
-                                                                         NS, Kp, As, rA * Kp, eA);
+                                                                         kc, NS, Kp, As, rA * Kp, eA);
     else
         slice_grouped_kernel<FMT_F32PAIR><<<gA, 32 * GATHER_WARPS, smem, s>>>(A, pl.offM0, pl.offK0, pl.groups,
-                                                                             pl.hdr, 0, NS, Kp, As, rA * Kp, eA);
+                                                                             pl.hdr, 0, kc, NS, Kp, As, rA * Kp, eA);
     if (bfmt == FMT_F64)
         slice_grouped_kernel<FMT_F64><<<gB, 32 * GATHER_WARPS, smem, s>>>(B, pl.offN0, pl.offK1, pl.groups, pl.hdr, 1,
-                                                                         NS, Kp, Bs, rB * Kp, eB);
+                                                                         0, NS, Kp, Bs, rB * Kp, eB);
     else
         slice_grouped_kernel<FMT_F32PAIR><<<gB, 32 * GATHER_WARPS, smem, s>>>(B, pl.offN0, pl.offK1, pl.groups,
-                                                                             pl.hdr, 1, NS, Kp, Bs, rB * Kp, eB);
+                                                                             pl.hdr, 1, 0, NS, Kp, Bs, rB * Kp, eB);
     HOTRG_COUNT(2);
     prof_end(ctx, h_slice, PROF_SLICE, 0.0);
     HOTRG_LAUNCH_CHECK(ctx, "slice_grouped_kernel");
@@ -1318,6 +1339,9 @@ hotrg_status umma_grouped(hotrg_ctx* ctx, int prec, const BsPlan& pl, const void
     a.eB = eB;
     a.rowC = pl.offM1;
     a.colC = pl.offN1;
+    a.pi = pl.pi_out;
+    a.rowP = pl.offM2;
+    a.colP = pl.offN2;
     a.C = C;
     a.status = st;
     // the tile width the plan's tile table was made for

@@ -176,18 +176,22 @@ constexpr int BS_VOFF = 64;     // value v is stored at slot v - centre + BS_VOF
 constexpr int BS_CHUNK = 256;   // elements per warp in the counting passes
 
 // One leg of an index set: its label array, extent, sign in the set's value,
-// and its element strides in the two tensors that use the set.
+// and its element strides in the two tensors that use the set; st2 is the leg's
+// stride in the index of a pair table (the output's value-sorted pair layout).
 struct BsFactor {
     const int32_t* lab;
     int64_t ext;
     int sgn;
     int64_t st0, st1;
+    int64_t st2;
 };
-// An index set of up to three legs, factor 0 the most significant digit.
+// An index set of up to three legs, factor 0 the most significant digit.  With
+// pi0 set, the first offset is a pair table entry: o0 = pi0[sum_f i_f st0_f].
 struct BsSet {
     int nf;
     BsFactor f[3];
     int64_t size;
+    const int32_t* pi0;
 };
 struct BsGroup {  // one charge block of a grouped contraction
     int64_t mbase, kbase, nbase;  // first positions in the sorted M / K / N lists
@@ -206,6 +210,14 @@ struct BsPlan {  // device pointers (workspace) plus the host-known set sizes
     int64_t *offM0, *offM1;  // M set: offsets in A, in C
     int64_t *offK0, *offK1;  // K set: offsets in A, in B
     int64_t *offN0, *offN1;  // N set: offsets in B, in C
+    // Output in a pair layout (pi_out set): element (m, n) goes to
+    // C[offM1[m] + offN1[n] + pi_out[offM2[m] + offN2[n]]].
+    const int32_t* pi_out;
+    int32_t *offM2, *offN2;
+    // The K set reads A through a pair table: each group's A-side K offsets are then
+    // consecutive (the table ranks the pairs of one value in the order the planner
+    // lists them), so a row's elements are one contiguous run.
+    int32_t kA_contig;
     int64_t nM, nK, nN;
     int32_t kp_cap;  // slice row pitch (>= every block's padded K; checked on the device)
     int32_t tile_n;  // output columns per tile of the tile table (128, or 64 for the split forms)
@@ -217,8 +229,13 @@ size_t bs_plan_bytes(int64_t nM, int64_t nK, int64_t nN);
 // HOTRG_ENOTSUP in the engine's status word.
 // kp_cap_override > 0 replaces the slice pitch limit (the FP64 engine slices nothing).
 // tile_n: output columns per tile of the tile table (rows are always 128).
+// pi_out: the output's pair table (null: the output offset is offM1 + offN1).
 hotrg_status bs_plan(hotrg_ctx* ctx, int sym, const BsSet& M, const BsSet& K, const BsSet& N, int prof_class,
-                     BsPlan& out, int32_t kp_cap_override = 0, int tile_n = 128);
+                     BsPlan& out, int32_t kp_cap_override = 0, int tile_n = 128, const int32_t* pi_out = nullptr);
+// Pair table of two legs a (labels qa, extent na) and b (qb, nb): pi[a nb + b] = the rank of
+// the pair (a, b) in the order of (value, a, b), value = qa[a] + qb[b] (its parity for Z2).
+// Pairs of one value then occupy one contiguous range, in the order the planner lists them.
+hotrg_status pair_table(hotrg_ctx* ctx, int sym, const int32_t* qa, int na, const int32_t* qb, int nb, int32_t* pi);
 // Slice row pitch of a grouped product: the whole K set rounded to 32 for small sets and
 // Z2; half of it (at least 4096) for larger U(1) sets (bs_plan checks every block on the device).
 int32_t bs_pitch(int64_t nK, int sym);
