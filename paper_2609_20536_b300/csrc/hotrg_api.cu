@@ -430,13 +430,13 @@ static hotrg_status coarse(hotrg_ctx* ctx, int prec, const double* P, int Dh, in
 //   s3  M = (x, u, d): q_x + q_u - q_d     K = (r1, r2): q_r1 + q_r2  N = x': q_x'
 // These are the charge rules of P (q_x = q_a + q_b) and T (q_l + q_u = q_r + q_d)
 // rewritten for each product, so every element a later product reads is
-// written by the earlier one.  Tc is zeroed first: s3 writes only its blocks.
-// Offsets: W and Z are laid out per the comment below; T, P, Tc as usual.
+// written by the earlier one.  T_out is zeroed first: s3 writes only its blocks.
+// Offsets: W and Z are laid out per the comment below; T and P as usual.
 // piW, piZ: workspace for the two pair tables (Dh Dv and Dh Dh entries).
 static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const double* P, const int32_t* qh,
                                   const int32_t* qv, const int32_t* qn, int Dh, int Dv, int Dp, const double* T_up,
-                                  const double* T_dn, double* W, double* Z, double* Tc, double* T_out,
-                                  int32_t* piW, int32_t* piZ) {
+                                  const double* T_dn, double* W, double* Z, double* T_out, int32_t* piW,
+                                  int32_t* piZ) {
     const int64_t h = Dh, v = Dv, p = Dp, hh = h * h, vv = v * v;
     hotrg_status s;
     // In the split forms W and Z are written and read as exact FP32 pairs (8 bytes, the value
@@ -477,17 +477,15 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
         BsSet N{2, {{qv, v, +1, 1, hh, 0}, {qh, h, +1, vv, 0, 1}}, v * h};
         if ((s = run(M, K, N, W, wf, T_dn, Z, wf, piZ)) != HOTRG_OK) return s;
     }
-    // s3: Tc[x][u][d][x'] = sum_{r1,r2} Z[x][u][d][piZ(r1,r2)] P[r1][r2][x']
-    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(Tc, 0, (size_t)p * vv * p * 8, ctx->stream));
+    // s3, written straight into the next step's axis order (no relabelling pass):
+    // T_out[u][d][x][x'] = sum_{r1,r2} Z[x][u][d][piZ(r1,r2)] P[r1][r2][x']
+    HOTRG_CUDA_TRY(ctx, cudaMemsetAsync(T_out, 0, (size_t)p * vv * p * 8, ctx->stream));
     {
-        BsSet M{3, {{qn, p, +1, vv * hh, vv * p}, {qv, v, +1, v * hh, v * p}, {qv, v, -1, hh, p}}, p * vv};
+        BsSet M{3, {{qn, p, +1, vv * hh, p}, {qv, v, +1, v * hh, v * p * p}, {qv, v, -1, hh, p * p}}, p * vv};
         BsSet K{2, {{qh, h, +1, h, h * p}, {qh, h, +1, 1, p}}, hh, piZ};
         BsSet N{1, {{qn, p, +1, 1, 1}}, p};
-        if ((s = run(M, K, N, Z, wf, P, Tc, 0, nullptr)) != HOTRG_OK) return s;
+        if ((s = run(M, K, N, Z, wf, P, T_out, 0, nullptr)) != HOTRG_OK) return s;
     }
-    // relabel for the other axis: T_out[u][d][x][x'] = Tc[x][u][d][x']
-    Perm po{4, {Dv, Dv, Dp, Dp}, {(int64_t)Dv * Dp, Dp, vv * Dp, 1}};
-    permute(ctx, Tc, T_out, po);
     return HOTRG_OK;
 }
 
@@ -570,7 +568,7 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
         return s;
     prof_end(ctx, h_eig, PROF_EIG, 0.0);
     if (blocks) {
-        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, Tc, T_out, piW, piZ)) !=
+        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, T_out, piW, piZ)) !=
             HOTRG_OK)
             return s;
     } else if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, T_out)) != HOTRG_OK) {
@@ -580,10 +578,10 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     if (Ti_in) {
         // T_imp' = [P^T (T_imp above T) P + P^T (T above T_imp) P] / (2 c_k)
         if (blocks) {
-            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Tc, Ti_out, piW, piZ)) !=
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Ti_out, piW, piZ)) !=
                 HOTRG_OK)
                 return s;
-            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Tc, Ti2, piW, piZ)) !=
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Ti2, piW, piZ)) !=
                 HOTRG_OK)
                 return s;
         } else {
