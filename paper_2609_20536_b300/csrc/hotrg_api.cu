@@ -471,7 +471,8 @@ static hotrg_status coarse_blocks(hotrg_ctx* ctx, int prec, int sym, const doubl
     }
     // s2: Z[x][u][d][piZ(r1,r2)] = sum_{l2,i} W[x][r1][u][piW(l2,i)] T_dn[l2][r2][i][d]
     {
-        BsSet M{3, {{qn, p, +1, hh * vv, vv * hh, 0}, {qh, h, -1, v * h * v, 0, h}, {qv, v, +1, h * v, v * hh, 0}},
+        BsSet M{3,
+                {{qn, p, +1, hh * vv, vv * hh, 0}, {qh, h, -1, v * h * v, 0, h}, {qv, v, +1, h * v, v * hh, 0}},
                 p * h * v};
         BsSet K{2, {{qh, h, +1, v, h * vv}, {qv, v, +1, 1, v}}, h * v, piW};
         BsSet N{2, {{qv, v, +1, 1, hh, 0}, {qh, h, +1, vv, 0, 1}}, v * h};
@@ -561,15 +562,16 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     // list at least twice the states they keep, so the iteration converges fast); with Z2 or no
     // symmetry it solves every block by Jacobi; eig_mode = 1 asks for Jacobi everywhere
     plan.exact = p->eig_mode == 1 || (prec == HOTRG_FP64 && plan.sym != SYM_U1);
-    plan.fp64_iters = p->eig_fp64_iters > 0 ? p->eig_fp64_iters : (p->eig_fp64_iters < 0 ? 0 : (prec == HOTRG_FP64 ? 6 : 0));
+    plan.fp64_iters =
+        p->eig_fp64_iters > 0 ? p->eig_fp64_iters : (p->eig_fp64_iters < 0 ? 0 : (prec == HOTRG_FP64 ? 6 : 0));
     const int h_eig = prof_begin(ctx);
     if ((s = eig_truncate(ctx, plan, EL, p->env_policy == 0 ? ER : nullptr, q_h, P, q_out, info, eigws)) !=
         HOTRG_OK)
         return s;
     prof_end(ctx, h_eig, PROF_EIG, 0.0);
     if (blocks) {
-        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, T_out, piW, piZ)) !=
-            HOTRG_OK)
+        if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, T_in, W, W2, T_out, piW,
+                               piZ)) != HOTRG_OK)
             return s;
     } else if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, T_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, T_out)) != HOTRG_OK) {
         return s;
@@ -578,11 +580,11 @@ static hotrg_status do_step(hotrg_ctx* ctx, const hotrg_params* p, const double*
     if (Ti_in) {
         // T_imp' = [P^T (T_imp above T) P + P^T (T above T_imp) P] / (2 c_k)
         if (blocks) {
-            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Ti_out, piW, piZ)) !=
-                HOTRG_OK)
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, Ti_in, T_in, W, W2, Ti_out, piW,
+                                   piZ)) != HOTRG_OK)
                 return s;
-            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Ti2, piW, piZ)) !=
-                HOTRG_OK)
+            if ((s = coarse_blocks(ctx, prec, sym, P, q_h, q_v, q_out, Dh, Dv, Dp, T_in, Ti_in, W, W2, Ti2, piW,
+                                   piZ)) != HOTRG_OK)
                 return s;
         } else {
             if ((s = coarse(ctx, prec, P, Dh, Dv, Dp, Ti_in, T_in, Pt, Pt2, Tt, Tb, W, W2, Tc, Ti_out)) != HOTRG_OK)

@@ -476,7 +476,8 @@ __device__ void cgs2_warp_t(float* Yt, int m, int b, uint32_t salt, float dep_to
         bool done = false;
         for (int attempt = 0; attempt < 4 && !done; ++attempt) {
             if (attempt > 0) {
-                for (int t = lane; t < m; t += 32) yj[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)j);
+                for (int t = lane; t < m; t += 32)
+                    yj[t] = hash_unit((uint32_t)t + 7919u * (salt + (uint32_t)attempt), (uint32_t)j);
                 __syncwarp();
             }
             float n0 = 0.f;
@@ -955,7 +956,8 @@ __device__ void chol_upper_warp(double* G, int b, int* live, double* rinv) {
             live[j] = ok ? 1 : 0;
             rinv[j] = ri;
         }
-        for (int c = j + lane; c < b; c += 32) G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] * ri) : (c == j ? 1.0 : 0.0);
+        for (int c = j + lane; c < b; c += 32)
+            G[j * b + c] = ok ? (c == j ? rjj : G[j * b + c] * ri) : (c == j ? 1.0 : 0.0);
         __syncwarp();
         // trailing update: G[r][c] -= R[j][r] R[j][c] for j < r <= c
         for (int idx = lane; idx < b * b; idx += 32) {
@@ -1339,7 +1341,8 @@ __global__ void projector_kernel(int dprime, int policy, double side_rtol, EigWs
     const int64_t aoff = w.sec_aoff[sct];
     if (b == m) {  // a Jacobi block: its eigenvectors are stored
         const double* V = w.V[side] + aoff;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) P[(int64_t)w.members[start + i] * dprime + j] = V[(int64_t)i * b + pos];
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            P[(int64_t)w.members[start + i] * dprime + j] = V[(int64_t)i * b + pos];
     } else {  // a subspace block: Ritz vector Q W[:, pos] (Q in S2, m x b; W in S1, b x b)
         const double* Q = w.S2[side] + aoff;
         const double* Wc = w.S1[side] + aoff + pos;
