@@ -51,3 +51,14 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], rank=1)
     assert r.returncode == 0, r.stderr[-2000:]
     assert json_lines(r.stdout) == []
+
+
+def test_single_core_sample_runs_on_one_thread():
+    # the bench's cpu_baseline.single_core: the nx = 1 sample in a child process with one-thread pools
+    import bench
+    from paper_2609_20536_b300.workloads import headline_points
+    p = headline_points(1, d_cut=bench.D_CUT, n_max=bench.N_MAX, n_steps=bench.N_STEPS)[0]
+    out = bench.oracle_sample_one_thread(p.beta, p.delta)
+    assert out is not None
+    s1, u1, threads = out
+    assert threads == 1 and s1 > 0 and 0 < u1 < 1
